@@ -1,0 +1,166 @@
+"""Seeded synthetic workloads: configuration dicts and initial fields.
+
+Shared by the CUDA path's tests and benchmark and by the CPU oracle. This module
+holds geometry and parameter bookkeeping only -- no equation of state, no lattice
+arithmetic. Thermodynamic inputs (T_c, coexistence densities, sigma) are passed in
+by the caller, each side computing them with its own code.
+
+Configuration dict schema (all lattice units; side order x-min, x-max, y-min, y-max):
+
+  nx, ny                 grid size; node (x, y) is stored at [y][x]
+  a, b, R, omega, G      Peng-Robinson EOS and pseudopotential strength (G < 0)
+  s[9]                   MRT rates (diagonal of Lambda) in the order of M's rows
+  eta_l, eta_v           kinematic viscosities; both > 0 => s[7], s[8] from eta(rho)
+  rho_l, rho_v           anchors of the eta(rho) and lambda(rho) interpolations
+  sigma, kappa           Li thermodynamic-consistency and surface-tension parameters
+  gx, gy                 gravity (body force g (rho - rho_bar))
+  cv, lambda_l, lambda_v energy equation
+  energy_on, iso_steps   energy equation switch; held isothermal for the first iso_steps
+  hydro_bc[4]            PERIODIC | WALL | OUTFLOW
+  thermal_bc[4]          T_PERIODIC | T_DIRICHLET | T_ADIABATIC
+  T_side[4], rho_w_side[4]   per-side Dirichlet temperature and wall density
+  rho_w[4], T_w[4], T_dirichlet[4]   optional per-boundary-node arrays (None = per side)
+  precision, rho_ref     CUDA path only: "fp64" | "fp32"; reference density of the
+                         FP32 deviation storage
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PERIODIC, WALL, OUTFLOW = 0, 1, 2
+T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
+
+# rates of the droplet/Stefan/pool runs (Sec. 4.2 and 4.3 of the paper): rho, e, zeta, j, q, j, q, eta, eta
+RATES_STEFAN_POOL = [1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25]
+
+
+def base_config(nx: int, ny: int, **kw) -> dict:
+    cfg = dict(
+        nx=int(nx), ny=int(ny),
+        a=3.0 / 49.0, b=2.0 / 21.0, R=1.0, omega=0.344, G=-1.0,
+        s=[1.0] * 9,
+        eta_l=0.0, eta_v=0.0, rho_l=7.0, rho_v=0.2,
+        sigma=0.0, kappa=0.0, gx=0.0, gy=0.0,
+        cv=5.0, lambda_l=2.0 / 3.0, lambda_v=2.0 / 3.0,
+        energy_on=0, iso_steps=0,
+        hydro_bc=[PERIODIC] * 4, thermal_bc=[T_PERIODIC] * 4,
+        T_side=[0.0] * 4, rho_w_side=[0.0] * 4,
+        rho_w=[None] * 4, T_w=[None] * 4, T_dirichlet=[None] * 4,
+        precision="fp64", rho_ref=1.0,
+    )
+    for k, v in kw.items():
+        if k not in cfg:
+            raise KeyError("unknown config key %r" % k)
+        cfg[k] = v
+    return cfg
+
+
+def _tanh_profile(inside: float, outside: float, dist_inside, width: float):
+    """0.5 (in + out) + 0.5 (in - out) tanh(2 d / W), d > 0 inside the region."""
+    return 0.5 * (inside + outside) + 0.5 * (inside - outside) * np.tanh(2.0 * dist_inside / width)
+
+
+def droplet_fields(nx, ny, R0, width, rho_in, rho_out, T_in, T_out, cx=None, cy=None):
+    """Circular region of radius R0 centred in the domain (Sec. 4.1 initial profile,
+    liquid inside)."""
+    cx = (nx - 1) / 2.0 if cx is None else cx
+    cy = (ny - 1) / 2.0 if cy is None else cy
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+    rho = _tanh_profile(rho_in, rho_out, R0 - d, width)
+    T = _tanh_profile(T_in, T_out, R0 - d, width)
+    z = np.zeros((ny, nx))
+    return rho, z.copy(), z.copy(), T
+
+
+def slab_fields(nx, ny, x0, x1, width, rho_in, rho_out, T):
+    """Liquid slab x0 < x < x1 across a periodic strip (planar interfaces)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    d = np.minimum(x - x0, x1 - x)
+    rho = _tanh_profile(rho_in, rho_out, d, width)
+    z = np.zeros((ny, nx))
+    return rho, z.copy(), z.copy(), np.full((ny, nx), float(T))
+
+
+def static_droplet(Tc, rho_v, rho_l, nx=64, ny=64, R0=16.0, width=3.0, T_ratio=0.8, sigma=0.1,
+                   kappa=0.0, precision="fp64"):
+    """Isothermal static droplet, periodic, all rates 1 (tau = 1)."""
+    T = T_ratio * Tc
+    cfg = base_config(nx, ny, sigma=sigma, kappa=kappa, rho_l=rho_l, rho_v=rho_v, precision=precision,
+                      rho_ref=rho_v)
+    return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T, T)
+
+
+def stefan_strip(Tc, rho_v, rho_l, sigma, nx=1024, ny=4, n_vapour=10, dT_ratio=0.05, T_ratio=0.86,
+                 cv=10.0, lambda_v=1.0, lambda_l=10.0, width=2.0, precision="fp64"):
+    """1-D boiling-like Stefan strip (Sec. 4.2): psi-based hydrophobic wall at x = 0
+    (rho_w = rho_v) held at T_sat + dT, zero-gradient outflow at x = nx-1, y periodic,
+    vapour layer of n_vapour nodes, liquid at T_sat elsewhere."""
+    T_sat = T_ratio * Tc
+    cfg = base_config(
+        nx, ny, s=list(RATES_STEFAN_POOL), eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v,
+        sigma=sigma, cv=cv, lambda_l=lambda_l, lambda_v=lambda_v, energy_on=1,
+        hydro_bc=[WALL, OUTFLOW, PERIODIC, PERIODIC],
+        thermal_bc=[T_DIRICHLET, T_ADIABATIC, T_PERIODIC, T_PERIODIC],
+        T_side=[T_sat + dT_ratio * Tc, 0.0, 0.0, 0.0], rho_w_side=[rho_v, 0.0, 0.0, 0.0],
+        precision=precision, rho_ref=rho_l)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    rho = _tanh_profile(rho_l, rho_v, x - n_vapour, width)
+    z = np.zeros((ny, nx))
+    return cfg, (rho, z.copy(), z.copy(), np.full((ny, nx), T_sat))
+
+
+def droplet_vaporization(Tc, rho_v, rho_l, sigma, nx=256, ny=256, R0=40.0, width=3.0, T_ratio=0.8,
+                         Tv_ratio=0.9, kappa=0.3, iso_steps=10000, precision="fp64"):
+    """Droplet in superheated vapour (Sec. 4.1): periodic hydrodynamics, temperature held
+    at T_v on the boundary ring, isothermal for the first iso_steps."""
+    T_l, T_v = T_ratio * Tc, Tv_ratio * Tc
+    cfg = base_config(
+        nx, ny, s=[1.25] * 9, eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v, sigma=sigma,
+        kappa=kappa, cv=5.0, lambda_l=2.0 / 3.0, lambda_v=2.0 / 3.0, energy_on=1, iso_steps=iso_steps,
+        thermal_bc=[T_DIRICHLET] * 4, T_side=[T_v] * 4, precision=precision, rho_ref=rho_v)
+    return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T_l, T_v)
+
+
+def pool_boiling(Tc, rho_v, rho_l, sigma, nx=1024, ny=2048, g=3e-5, T_ratio=0.86, heater_frac=0.2,
+                 dTh_ratio=0.1, rho_w_heater=3.44, rho_w_bottom=6.50, rho_w_top=0.38,
+                 pool_frac=2.0 / 3.0, noise_ratio=1e-3, seed=20220112, width=3.0, precision="fp64"):
+    """2-D pool boiling (Sec. 4.3): x periodic, Zou-He walls at y = 0 and y = ny-1,
+    bottom-centre heater strip of heater_frac * nx nodes held at T_sat + dTh (Dirichlet),
+    adiabatic elsewhere; psi-based wall densities per wall node; liquid pool below
+    pool_frac * ny at T_sat with seeded uniform noise of +-noise_ratio * Tc."""
+    T_sat = T_ratio * Tc
+    T_h = T_sat + dTh_ratio * Tc
+    w = max(1, int(round(heater_frac * nx)))
+    x0 = (nx - w) // 2
+    heater = np.zeros(nx, dtype=np.uint8)
+    heater[x0:x0 + w] = 1
+    rho_w_b = np.where(heater == 1, rho_w_heater, rho_w_bottom).astype(np.float64)
+    T_w_b = np.where(heater == 1, T_h, T_sat).astype(np.float64)
+    cfg = base_config(
+        nx, ny, s=list(RATES_STEFAN_POOL), eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v,
+        sigma=sigma, gx=0.0, gy=-g, cv=5.0, lambda_l=1.95, lambda_v=0.114, energy_on=1,
+        hydro_bc=[PERIODIC, PERIODIC, WALL, WALL],
+        thermal_bc=[T_PERIODIC, T_PERIODIC, T_ADIABATIC, T_ADIABATIC],
+        T_side=[0.0, 0.0, T_sat, T_sat], rho_w_side=[0.0, 0.0, rho_w_bottom, rho_w_top],
+        rho_w=[None, None, rho_w_b, None], T_w=[None, None, T_w_b, None],
+        T_dirichlet=[None, None, heater, None], precision=precision, rho_ref=rho_l)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    rho = _tanh_profile(rho_l, rho_v, pool_frac * ny - y, width)
+    rng = np.random.default_rng(seed)
+    T = T_sat + noise_ratio * Tc * rng.uniform(-1.0, 1.0, size=(ny, nx))
+    z = np.zeros((ny, nx))
+    return cfg, (rho, z.copy(), z.copy(), T)
+
+
+def random_smooth_density(nx, ny, rho_lo, rho_hi, seed, modes=3):
+    """Smooth periodic random density field in [rho_lo, rho_hi] (a few Fourier modes)."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    acc = np.zeros((ny, nx))
+    for _ in range(modes):
+        kx, ky = rng.integers(1, 3, size=2)
+        ph = rng.uniform(0, 2 * np.pi, size=2)
+        acc += np.cos(2 * np.pi * kx * x / nx + ph[0]) * np.cos(2 * np.pi * ky * y / ny + ph[1])
+    acc = (acc - acc.min()) / (acc.max() - acc.min())
+    return rho_lo + (rho_hi - rho_lo) * acc
