@@ -1,0 +1,274 @@
+"""Benchmark of the fused coupled LBM + energy step on GB300.
+
+Workload (synthetic, seeded): 2-D pool boiling on a 2048 x 4096 grid (x periodic, Zou-He
+psi-based walls at y = 0 and y = ny-1, bottom heater strip of nx/5 at T_sat + 0.1 Tc,
+adiabatic elsewhere, liquid pool below 2/3 of the height, +-1e-3 Tc temperature noise,
+g = 3e-5, PR EOS a = 3/49, sigma = 0.103). One bench step = one time step of the whole
+grid (one fused kernel launch). Metric: coupled LBM + energy MLUPS of the FP32 path
+(populations stored as f_i - w_i rho_ref), with the FP64 path measured beside it.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]  (N > 1 under torch.distributed.run:
+each rank advances its own replica; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 2048, 4096
+SIGMA = 0.103  # Table 2, base mesh (a = 6.12e-2 = 3/49) at T_sat = 0.86 Tc
+BYTES_PER_NODE = {"fp32": 80, "fp64": 160}  # read + write of 9 populations and T
+
+
+def workload(precision: str, nx=NX, ny=NY, thermo="product"):
+    import workloads as W
+    a, b, R, omega = 3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344
+    if thermo == "product":
+        from paper_2201_04560_gb300 import ppl
+        Tc = ppl.tc(a, b, R)
+        rv, rl, _ = ppl.maxwell(a, b, R, omega, 0.86 * Tc)
+    else:
+        from oracle import thermo as th
+        e = th.PR(a=a, b=b, R=R, omega=omega)
+        Tc = e.Tc
+        rv, rl, _ = th.maxwell(e, 0.86 * Tc)
+    return W.pool_boiling(Tc, rv, rl, SIGMA, nx=nx, ny=ny, g=3e-5, precision=precision)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def time_device(sim, steps, warmup, torch):
+    """Device time of `steps` fused steps (CUDA events on the launching stream)."""
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream)
+    sim.step_async(warmup)
+    sim.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sim.launch_count
+    torch.cuda.synchronize()
+    start.record(stream)
+    sim.step_async(steps)
+    end.record(stream)
+    end.synchronize()
+    sim.sync()
+    return start.elapsed_time(end) / 1e3, sim.launch_count - l0
+
+
+def cpu_oracle_sample(steps=3):
+    """The FP64 C oracle, single-threaded, on the same workload for a few steps."""
+    from oracle import oracle
+    cfg, ic = workload("fp64", thermo="oracle")
+    o = oracle.Oracle(cfg, *ic)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": NX * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d pool boiling, %d FP64 steps, single-threaded C oracle" % (NX, NY, steps)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+    nx, ny = 512, 1024
+    cfg, ic = workload("fp64", nx=nx, ny=ny, thermo="oracle")
+    o = oracle.Oracle(cfg, *ic)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = nx * ny * args.steps / dt / 1e6
+    sample = "%dx%d crop of the pool-boiling workload, FP64 C oracle, single-threaded" % (nx, ny)
+    print(json.dumps({
+        "impl": "reference", "metric": "coupled LBM+energy MLUPS", "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "pool boiling %dx%d (crop of %dx%d)" % (nx, ny, NX, NY), "grid": [nx, ny]},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=32)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=0, help="FP64 timed steps (default steps/8, >= 8)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2201_04560_gb300 import Simulation
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    nodes = NX * NY
+    peaks, peak_kind = measured_peaks()
+    out = {}
+    for prec in ("fp32", "fp64"):
+        steps = args.steps if prec == "fp32" else (args.fp64_steps or max(8, args.steps // 8))
+        cfg, ic = workload(prec)
+        sim = Simulation(cfg, *ic)
+        sampler = ClockSampler(local) if prec == "fp32" else None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        dt, launches = time_device(sim, steps, args.warmup, torch)
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        dt = max_over_ranks(dt)
+        n = sim.norms()
+        out[prec] = {"dt": dt, "steps": steps, "launches": launches, "clocks": clocks, "flags": n["flags"],
+                     "mass": n["mass"]}
+        if prec == "fp32":
+            # end to end through the C ABI: pinned host inputs -> device, K steps, fields -> host
+            host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory() for a in ic]
+            host_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+            import ctypes
+            P = ctypes.POINTER(ctypes.c_double)
+            sim.set_stream(None)
+            barrier()
+            t0 = time.perf_counter()
+            rc = sim.lib.ppl_reset(sim.h, *[ctypes.cast(t.data_ptr(), P) for t in host_in])
+            assert rc == 0, rc
+            sim.step(steps)
+            rc = sim.lib.ppl_fields(sim.h, *[ctypes.cast(t.data_ptr(), P) for t in host_out])
+            assert rc == 0, rc
+            e2e_dt = max_over_ranks(time.perf_counter() - t0)
+            out["e2e"] = {"value": world * nodes * steps / e2e_dt / 1e6, "unit": "MLUPS",
+                          "h2d_bytes_per_step": int(4 * nodes * 8 / steps),
+                          "d2h_bytes_per_step": int(4 * nodes * 8 / steps)}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    f32, f64 = out["fp32"], out["fp64"]
+    mlups32 = world * nodes * f32["steps"] / f32["dt"] / 1e6
+    mlups64 = world * nodes * f64["steps"] / f64["dt"] / 1e6
+    per_launch32 = f32["dt"] / f32["steps"]
+    per_launch64 = f64["dt"] / f64["steps"]
+    ach32 = BYTES_PER_NODE["fp32"] * nodes / per_launch32 / 1e9
+    ach64 = BYTES_PER_NODE["fp64"] * nodes / per_launch64 / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    line = {
+        "metric": "coupled LBM+energy MLUPS (FP32 vs FP64, same GB300) and % of HBM roofline",
+        "value": mlups32, "unit": "MLUPS", "n_gpus": world, "steps": f32["steps"], "warmup": args.warmup,
+        "ms_per_step": per_launch32 * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "pool boiling %dx%d, FP32 populations as f - w rho_ref" % (NX, NY),
+                   "grid": [NX, NY], "l2": "state (335 MB FP32, 671 MB FP64 per buffer) larger than L2",
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
+                     "traffic": None, "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
+        "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,
+                 "roofline": {"bound": "alu", "achieved_gbs": ach64, "hbm_frac": ach64 / hbm,
+                              "bytes_per_node": BYTES_PER_NODE["fp64"]}},
+        "e2e": out["e2e"],
+        "gpu_launches": f32["launches"],
+        "clocks": f32["clocks"],
+        "status_flags": {"fp32": f32["flags"], "fp64": f64["flags"]},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

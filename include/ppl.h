@@ -1,0 +1,202 @@
+/*
+ * ppl -- GB300-native pseudopotential lattice Boltzmann library for boiling heat transfer.
+ *
+ * C ABI of the hot path of arXiv 2201.04560 (Jaramillo, Mapelli, Cabezas-Gomez,
+ * "Pseudopotential Lattice Boltzmann Method for boiling heat transfer: a mesh refinement
+ * procedure"): one fused per-node update of the D2Q9 MRT pseudopotential LBM (Sec. 2,
+ * Eqs. lbm, collisionMRT, EquilibriumDistribution, DensityAndVelocityRelationToF), the
+ * Peng-Robinson pseudopotential (Eqs. psi, peng-robinson), the Shan-Chen force with the
+ * psi-based wall adhesion (Eqs. shanchen, shanchen-walls, psi-based-formula), gravity
+ * (Eq. gravitational_force), the Li sigma/kappa source terms (Eqs. li_source_terms, S,
+ * surface-tension-correction-term-C/-Q, Q-psi-based), Zou-He wet-node walls and the
+ * hybrid finite-difference temperature equation (Eq. energy-equation) advanced by a
+ * second-order Runge-Kutta (Heun) step.
+ *
+ * Conventions
+ *  - All values are lattice units. Fields are row-major [ny][nx]: node (x, y) is element
+ *    y*nx + x. Populations are [9][ny][nx] in the velocity order of Sec. 2:
+ *    c = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *  - Boundary sides are indexed 0 = x-min, 1 = x-max, 2 = y-min, 3 = y-max. At most one
+ *    axis may be non-periodic for the hydrodynamics (no wall corners).
+ *  - Every entry point returns PPL_OK (0) or a negative PPL_E_* code; nothing throws
+ *    across the ABI. ppl_strerror() names a code. Thread safety: one handle must not be
+ *    used from two host threads at once; distinct handles are independent.
+ *  - Ownership: the library owns all device memory of a handle (freed by ppl_destroy).
+ *    Host and device buffers passed in are caller-owned, only read or written during the
+ *    call, and must stay valid for its duration. ppl_init copies the configuration,
+ *    including the optional per-node boundary arrays.
+ *  - Asynchrony: work is enqueued on the handle's stream (default: the legacy default
+ *    stream; see ppl_set_stream). ppl_step, ppl_fields*, ppl_norms, ppl_save and
+ *    ppl_populations synchronise that stream before they return.
+ */
+#ifndef PPL_H
+#define PPL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define PPL_OK 0
+#define PPL_E_INVAL (-1)   /* bad size, parameter or boundary combination; psi undefined at init */
+#define PPL_E_CUDA (-2)    /* a CUDA runtime call failed (no device, launch failure, ...) */
+#define PPL_E_NUMERIC (-3) /* the device status word reports NaN, rho <= 0 or a negative psi argument */
+#define PPL_E_TIMEOUT (-4) /* a bounded device wait ran out */
+#define PPL_E_IO (-5)      /* checkpoint file missing, short, or written by another configuration */
+#define PPL_E_NOMEM (-6)   /* device or host allocation failed */
+
+/* ---- enumerations ---- */
+#define PPL_FP64 0    /* populations and arithmetic in FP64 */
+#define PPL_FP32DEV 1 /* FP32 arithmetic; populations stored as f_i - w_i rho_ref in FP32 */
+
+#define PPL_PERIODIC 0 /* hydrodynamic side kinds */
+#define PPL_WALL 1     /* Zou-He no-slip wet node + psi-based adhesion (Sec. 2.2) */
+#define PPL_OUTFLOW 2  /* zero-gradient (null Neumann) copy of the first interior line */
+
+#define PPL_T_PERIODIC 0  /* thermal side kinds */
+#define PPL_T_DIRICHLET 1 /* boundary nodes held at T_side / T_w */
+#define PPL_T_ADIABATIC 2 /* mirror ghost across the wall row (zero normal gradient) */
+
+#define PPL_CONTACT_PSI 0 /* psi-based contact angle model (Eq. psi-based-formula) */
+
+/* status-word bits (ppl_norms.flags) */
+#define PPL_FLAG_PSI_NEG 1u /* 2 (p_EOS - rho/3) / G < 0 somewhere: psi undefined */
+#define PPL_FLAG_NAN 2u     /* NaN or Inf in rho or T */
+#define PPL_FLAG_RHO_NONPOS 4u
+
+/*
+ * Simulation configuration (Sec. 2 model parameters; Sec. 3 scaling is applied by the caller).
+ *  nx, ny        grid size (nx, ny >= 3; a non-periodic axis needs >= 4 nodes)
+ *  precision     PPL_FP64 or PPL_FP32DEV
+ *  rho_ref       reference density of the FP32 deviation storage (ignored for FP64)
+ *  a, b, R, omega  Peng-Robinson EOS (Eq. peng-robinson); T_c = 0.0778 a / (0.45724 b R)
+ *  G             pseudopotential strength of Eq. (psi), must be < 0 (the paper uses -1)
+ *  s[9]          diagonal of Lambda in the row order of M: s_rho, s_e, s_zeta, s_j, s_q, s_j, s_q, s_eta, s_eta
+ *  eta_l, eta_v  if both > 0, s_eta = 1/(3 eta(rho) + 1/2) per node with eta(rho) linear
+ *                between (rho_v, eta_v) and (rho_l, eta_l) (Eq. eta-rho); else s[7], s[8] are used
+ *  rho_l, rho_v  anchors of the eta(rho) and lambda(rho) interpolations (rho_l != rho_v)
+ *  sigma, kappa  Li thermodynamic-consistency and surface-tension parameters (Eqs. S, Q)
+ *  gx, gy        gravity of Eq. (gravitational_force), F^b = g (rho - rho_bar)
+ *  cv, lambda_l, lambda_v   energy equation (Eq. energy-equation), lambda linear in rho
+ *  energy_on     0: temperature frozen; 1: advanced from step iso_steps on
+ *  hydro_bc[4], thermal_bc[4]  side kinds (PPL_PERIODIC.. and PPL_T_PERIODIC..)
+ *  T_side[4]     Dirichlet temperature per side; rho_w_side[4] wall density per side
+ *  rho_w[4], T_w[4], T_dirichlet[4]  optional per-boundary-node arrays (length ny for
+ *                sides 0/1, nx for sides 2/3; NULL = use the per-side value). T_dirichlet
+ *                marks each node Dirichlet (1) or adiabatic (0) on a wall side. At corners
+ *                the y-sides decide the thermal kind and value.
+ *  contact_model PPL_CONTACT_PSI (the only model of the hot path); G_w reserved
+ */
+typedef struct ppl_config {
+  int32_t nx, ny;
+  int32_t precision;
+  double rho_ref;
+  double a, b, R, omega, G;
+  double s[9];
+  double eta_l, eta_v, rho_l, rho_v;
+  double sigma, kappa, gx, gy, cv, lambda_l, lambda_v;
+  int32_t energy_on;
+  int64_t iso_steps;
+  int32_t hydro_bc[4], thermal_bc[4];
+  double T_side[4];
+  double rho_w_side[4];
+  const double *rho_w[4];
+  const double *T_w[4];
+  const uint8_t *T_dirichlet[4];
+  int32_t contact_model;
+  double G_w;
+} ppl_config;
+
+/* FP64 diagnostics of the current state (the denominators of the space-time norms of
+ * Eqs. rel-diff-timestep and global-rel-diff are sum_abs_rho and sum_abs_T). */
+typedef struct ppl_norms_t {
+  int64_t step;
+  double mass;     /* sum of rho over all nodes */
+  double rho_mean; /* mass / (nx ny): the rho_bar of the next step's F^b */
+  double sum_abs_rho, sum_abs_T;
+  double rho_min, rho_max, T_min, T_max;
+  uint32_t flags; /* PPL_FLAG_* accumulated since init */
+} ppl_norms_t;
+
+typedef struct ppl_sim ppl_t;
+
+/* Allocate device state and initialise it: f = f^eq(rho0, u0) (Eq. EquilibriumDistribution),
+ * T = T0; Dirichlet nodes take their wall value and an outflow line copies the first
+ * interior line. rho0, ux0, uy0, T0: host FP64 [ny][nx]. Returns PPL_E_INVAL for bad
+ * sizes or parameters, or when psi is undefined (Eq. psi) anywhere in the initial state.
+ * On success *out owns the handle (release with ppl_destroy). */
+int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const double *uy0,
+             const double *T0, ppl_t **out);
+
+/* Re-initialise the state of an existing handle from host fields (as ppl_init, no
+ * allocation); the step counter restarts at 0. */
+int ppl_reset(ppl_t *h, const double *rho0, const double *ux0, const double *uy0, const double *T0);
+
+/* Enqueue all further work of h on `cuda_stream` (a cudaStream_t, e.g. a PyTorch stream's
+ * handle; NULL = legacy default stream). The stream must outlive its use by h. */
+int ppl_set_stream(ppl_t *h, void *cuda_stream);
+
+/* Advance nsteps >= 0 time steps (one fused kernel launch per step, replayed from CUDA
+ * graphs in chunks), then synchronise the stream and check the device status word:
+ * PPL_E_NUMERIC if any flag is set. */
+int ppl_step(ppl_t *h, int64_t nsteps);
+
+/* As ppl_step but returns right after enqueueing; no status check, no synchronisation. */
+int ppl_step_async(ppl_t *h, int64_t nsteps);
+
+/* Synchronise the stream and check the status word (pairs with ppl_step_async). */
+int ppl_sync(ppl_t *h);
+
+/* Macroscopic fields of the current state into caller-owned host FP64 [ny][nx] buffers:
+ * rho, u = (sum_i f_i c_i + F/2)/rho (Eq. DensityAndVelocityRelationToF) and T. Any
+ * pointer may be NULL to skip that field. */
+int ppl_fields(ppl_t *h, double *rho, double *ux, double *uy, double *T);
+
+/* As ppl_fields into caller-owned DEVICE buffers (e.g. torch data_ptr()s), each [ny][nx]
+ * of dtype 0 = FP64 or 1 = FP32; written on the handle's stream, synchronised on return. */
+int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtype);
+
+/* Populations of the current state (post-streaming, boundary conditions applied) as host
+ * FP64 [9][ny][nx], decoded from the FP32 deviation storage when precision is FP32DEV. */
+int ppl_populations(ppl_t *h, double *f);
+
+/* FP64 diagnostics of the current state; synchronises. */
+int ppl_norms(ppl_t *h, ppl_norms_t *out);
+
+/* Checkpoint: write / restore the full state (populations, T, rho_bar, step counter) with
+ * a header carrying the grid, precision and a hash of the configuration. ppl_load on a
+ * handle with a different configuration returns PPL_E_IO. A resumed run is bit-identical
+ * to an uninterrupted one. */
+int ppl_save(ppl_t *h, const char *path);
+int ppl_load(ppl_t *h, const char *path);
+
+/* Number of fused step kernels launched by this handle since init (for launch accounting). */
+int64_t ppl_launch_count(const ppl_t *h);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void ppl_destroy(ppl_t *h);
+
+/* Static description of a return code. */
+const char *ppl_strerror(int code);
+
+/* ---- host helpers of the refinement procedure (Sec. 3), FP64 ---- */
+
+/* Critical temperature of the Peng-Robinson EOS: T_c = 0.0778 a / (0.45724 b R) (Sec. 2.1). */
+double ppl_tc(double a, double b, double R);
+
+/* Maxwell equal-area coexistence of the PR isotherm at T < T_c (the target of the sigma
+ * tuning of Sec. 3.2): writes rho_v, rho_l and p_sat. PPL_E_INVAL if T >= T_c or on bad
+ * parameters. */
+int ppl_maxwell(double a, double b, double R, double omega, double T, double *rho_v,
+                double *rho_l, double *p_sat);
+
+/* Eq. (a-deltax): a on a mesh of n nodes per length, from a_base on n_base nodes. */
+double ppl_refine_a(double a_base, int32_t n_base, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPL_H */

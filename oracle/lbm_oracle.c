@@ -28,7 +28,8 @@
  *    weights W = 1/3, 1/12.
  *  - rho_bar is the mean of rho^n over all nodes at the start of the step.
  *  - psi-based wall: every solid link of a wall node x uses psi(rho_w(x), T(x)).
- *  - Zou-He no-slip closure without force (sum_i f_i c_i = 0 at the wall node).
+ *  - Zou-He no-slip closure with the half-force momentum sum_i f_i c_i = -F/2, F being
+ *    the wall node's force of the step that streamed the populations in.
  *  - Outflow (zero gradient): after streaming, all f and T of the outflow column are
  *    copies of the first interior column; neighbours beyond it are copies too.
  *  - FD stencils: d_a th = 3 sum_i w_i c_ia th(x+c_i), lap th = 6 sum_i w_i (th(x+c_i)-th(x)),
@@ -370,24 +371,29 @@ static long macro(const orc_params *P, const double *f, const double *T, work_t 
   return 0;
 }
 
-static void zou_he(int side, double *fl) {
-  /* no-slip wet node, unforced closure: unknowns = populations entering from the solid */
+/* Zou-He no-slip wet node: the populations entering from the solid are closed by
+ * bounce-back of the normal non-equilibrium part and by prescribing the population
+ * momentum J = sum_i f_i c_i. No slip with the half-force velocity of
+ * Eq. (DensityAndVelocityRelationToF) means J = -F/2; F is the force of the step that
+ * produced these populations (the wall node's own F at the new time would make the
+ * closure implicit in rho_wall and in its neighbours). */
+static void zou_he(int side, double *fl, double Jx, double Jy) {
   if (side == 2) {        /* y-min: unknown 2, 5, 6 */
-    fl[2] = fl[4];
-    fl[5] = fl[7] - 0.5 * (fl[1] - fl[3]);
-    fl[6] = fl[8] + 0.5 * (fl[1] - fl[3]);
+    fl[2] = fl[4] + 2.0 / 3.0 * Jy;
+    fl[5] = fl[7] - 0.5 * (fl[1] - fl[3]) + Jy / 6.0 + 0.5 * Jx;
+    fl[6] = fl[8] + 0.5 * (fl[1] - fl[3]) + Jy / 6.0 - 0.5 * Jx;
   } else if (side == 3) { /* y-max: unknown 4, 7, 8 */
-    fl[4] = fl[2];
-    fl[7] = fl[5] + 0.5 * (fl[1] - fl[3]);
-    fl[8] = fl[6] - 0.5 * (fl[1] - fl[3]);
+    fl[4] = fl[2] - 2.0 / 3.0 * Jy;
+    fl[7] = fl[5] + 0.5 * (fl[1] - fl[3]) - Jy / 6.0 - 0.5 * Jx;
+    fl[8] = fl[6] - 0.5 * (fl[1] - fl[3]) - Jy / 6.0 + 0.5 * Jx;
   } else if (side == 0) { /* x-min: unknown 1, 5, 8 */
-    fl[1] = fl[3];
-    fl[5] = fl[7] - 0.5 * (fl[2] - fl[4]);
-    fl[8] = fl[6] + 0.5 * (fl[2] - fl[4]);
+    fl[1] = fl[3] + 2.0 / 3.0 * Jx;
+    fl[5] = fl[7] - 0.5 * (fl[2] - fl[4]) + Jx / 6.0 + 0.5 * Jy;
+    fl[8] = fl[6] + 0.5 * (fl[2] - fl[4]) + Jx / 6.0 - 0.5 * Jy;
   } else {                /* x-max: unknown 3, 6, 7 */
-    fl[3] = fl[1];
-    fl[6] = fl[8] - 0.5 * (fl[2] - fl[4]);
-    fl[7] = fl[5] + 0.5 * (fl[2] - fl[4]);
+    fl[3] = fl[1] - 2.0 / 3.0 * Jx;
+    fl[6] = fl[8] - 0.5 * (fl[2] - fl[4]) - Jx / 6.0 + 0.5 * Jy;
+    fl[7] = fl[5] + 0.5 * (fl[2] - fl[4]) - Jx / 6.0 - 0.5 * Jy;
   }
 }
 
@@ -493,7 +499,7 @@ long orc_step(const orc_params *P, double *f, double *T, int64_t step) {
       if (sd < 0) continue;
       double fl[9];
       for (int i = 0; i < 9; ++i) fl[i] = f[FI(i, x, y)];
-      zou_he(sd, fl);
+      zou_he(sd, fl, -0.5 * w.Fx[IDX(x, y)], -0.5 * w.Fy[IDX(x, y)]);
       for (int i = 0; i < 9; ++i) f[FI(i, x, y)] = fl[i];
     }
   for (int y = 0; y < P->ny; ++y)

@@ -1,0 +1,915 @@
+// Host side of libppl: the C ABI declared in include/ppl.h, device buffers, CUDA-graph
+// step chunks, and the auxiliary kernels (initial state, field export, FP64 norms).
+// The hot path is the fused step kernel of step_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ppl.h"
+#include "step_kernel.cuh"
+
+using namespace ppl_dev;
+
+namespace {
+
+constexpr int kGraphSteps = 32;  // steps per captured CUDA graph (even: ping-pong parity returns)
+
+// ---------------------------------------------------------------------------------
+// auxiliary kernels
+// ---------------------------------------------------------------------------------
+
+// Eq. (EquilibriumDistribution): f^eq_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
+// stored as the deviation f^eq_i - w_i rho_ref. Dirichlet nodes take their wall value.
+template <typename real>
+__global__ void init_state(const Params<real> P, const double *rho0, const double *ux0, const double *uy0,
+                           const double *T0, real *f, real *T) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.plane) return;
+  const int gx = (int)(k % P.nx), gy = (int)(k / P.nx);
+  const double r = rho0[k], ux = ux0[k], uy = uy0[k];
+  const double uu = ux * ux + uy * uy;
+  const double rr = (double)P.rho_ref;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const double w = q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const double cu = kCX[q] * ux + kCY[q] * uy;
+    const double fe = w * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    f[q * P.plane + k] = (real)(fe - w * rr);
+  }
+  real tv;
+  T[k] = t_fixed(P, gx, gy, &tv) ? tv : (real)T0[k];
+}
+
+// Per-node diagnostics of the stored state, reduced per block into 7 FP64 partials:
+// sum rho, sum |rho|, sum |T|, min rho, max rho, min T, max T. Also checks that psi is
+// defined everywhere (including the wall values psi(rho_w, T)).
+template <typename real>
+__global__ void stats_partials(const Params<real> P, const real *f, const real *T, double *part,
+                               unsigned *status) {
+  constexpr int NT = 256;
+  __shared__ double red[7][NT / 32];
+  double s[7] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300};
+  unsigned flags = 0;
+  for (long long k = (long long)blockIdx.x * NT + threadIdx.x; k < P.plane; k += (long long)gridDim.x * NT) {
+    const int gx = (int)(k % P.nx), gy = (int)(k / P.nx);
+    const double w = sum_weight(P, gx, gy);
+    if (w == 0.0) continue;
+    real d = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d += f[q * P.plane + k];
+    const real rho = P.rho_ref + d;
+    const real t = T[k];
+    const real arg = psi_arg(P, rho, t);
+    if (!(arg >= real(0))) flags |= FLAG_PSI_NEG;
+    const int ws = wall_side(P, gx, gy);
+    if (ws >= 0 && !(psi_arg(P, wall_rho_w(P, ws, gx, gy), t) >= real(0))) flags |= FLAG_PSI_NEG;
+    if (!(rho == rho) || !(t == t) || isinf((double)rho) || isinf((double)t)) flags |= FLAG_NAN;
+    if (!(rho > real(0))) flags |= FLAG_RHO_NONPOS;
+    s[0] += w * (double)rho;
+    s[1] += w * fabs((double)rho);
+    s[2] += w * fabs((double)t);
+    s[3] = fmin(s[3], (double)rho);
+    s[4] = fmax(s[4], (double)rho);
+    s[5] = fmin(s[5], (double)t);
+    s[6] = fmax(s[6], (double)t);
+  }
+  if (flags) atomicOr(status, flags);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int j = 0; j < 3; ++j) s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
+    s[3] = fmin(s[3], __shfl_down_sync(0xffffffffu, s[3], o));
+    s[4] = fmax(s[4], __shfl_down_sync(0xffffffffu, s[4], o));
+    s[5] = fmin(s[5], __shfl_down_sync(0xffffffffu, s[5], o));
+    s[6] = fmax(s[6], __shfl_down_sync(0xffffffffu, s[6], o));
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int j = 0; j < 7; ++j) red[j][threadIdx.x >> 5] = s[j];
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    const int j = threadIdx.x;
+    double v = red[j][0];
+    for (int w = 1; w < NT / 32; ++w) {
+      const double x = red[j][w];
+      v = j < 3 ? v + x : (j == 3 || j == 5 ? fmin(v, x) : fmax(v, x));
+    }
+    part[(long long)blockIdx.x * 7 + j] = v;
+  }
+}
+
+// fixed-order finalize of the partials: out = {sum rho, sum|rho|, sum|T|, min/max rho, min/max T};
+// stats[0] = rho_bar, stats[1] = mass
+__global__ void stats_finalize(const double *part, int nblk, double inv_nodes, double *out, double *stats) {
+  if (threadIdx.x != 0) return;
+  double s[7] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300};
+  for (int b = 0; b < nblk; ++b) {
+    const double *p = part + (long long)b * 7;
+    s[0] += p[0];
+    s[1] += p[1];
+    s[2] += p[2];
+    s[3] = fmin(s[3], p[3]);
+    s[4] = fmax(s[4], p[4]);
+    s[5] = fmin(s[5], p[5]);
+    s[6] = fmax(s[6], p[6]);
+  }
+  for (int j = 0; j < 7; ++j) out[j] = s[j];
+  if (stats) {
+    stats[0] = s[0] * inv_nodes;
+    stats[1] = s[0];
+  }
+}
+
+// rho, u = (sum f c + F/2)/rho and T at every node (the outflow line reads its copy)
+template <typename real>
+__global__ void export_fields(const Params<real> P, const real *f, const real *T, const double *stats,
+                              void *o_rho, void *o_ux, void *o_uy, void *o_T, int dtype) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.plane) return;
+  const int gx = (int)(k % P.nx), gy = (int)(k / P.nx);
+  const NodeMap c = map_node(P, gx, gy);
+  const long long kc = (long long)c.y * P.nx + c.x;
+  real fl[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) fl[q] = f[q * P.plane + kc];
+  real d = 0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) d += fl[q];
+  const real rho = P.rho_ref + d;
+  const real t = T[kc];
+  const real jx = fl[1] - fl[3] + fl[5] - fl[6] - fl[7] + fl[8];
+  const real jy = fl[2] - fl[4] + fl[5] + fl[6] - fl[7] - fl[8];
+  const real psi_c = sqrt(fmax(psi_arg(P, rho, t), real(0)));
+  const int ws = wall_side(P, gx, gy);
+  const real psi_w = ws >= 0 ? sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, gx, gy), t), real(0))) : real(0);
+  real sx = 0, sy = 0;
+  for (int q = 1; q < 9; ++q) {
+    const int nxp = gx + kCX[q], nyp = gy + kCY[q];
+    real pn;
+    if (beyond_wall(P, nxp, nyp)) {
+      pn = psi_w;
+    } else {
+      const NodeMap m = map_node(P, nxp, nyp);
+      const long long kn = (long long)m.y * P.nx + m.x;
+      real dn = 0;
+      for (int r = 0; r < 9; ++r) dn += f[r * P.plane + kn];
+      pn = sqrt(fmax(psi_arg(P, P.rho_ref + dn, T[kn]), real(0)));
+    }
+    const real w = q < 5 ? real(1) / real(3) : real(1) / real(12);
+    sx += w * pn * real(kCX[q]);
+    sy += w * pn * real(kCY[q]);
+  }
+  const real rho_bar = (real)stats[0];
+  const real Fx = -P.G * psi_c * sx + P.gx * (rho - rho_bar);
+  const real Fy = -P.G * psi_c * sy + P.gy * (rho - rho_bar);
+  const real ux = (jx + real(0.5) * Fx) / rho, uy = (jy + real(0.5) * Fy) / rho;
+  if (dtype == 0) {
+    if (o_rho) ((double *)o_rho)[k] = (double)rho;
+    if (o_ux) ((double *)o_ux)[k] = (double)ux;
+    if (o_uy) ((double *)o_uy)[k] = (double)uy;
+    if (o_T) ((double *)o_T)[k] = (double)t;
+  } else {
+    if (o_rho) ((float *)o_rho)[k] = (float)rho;
+    if (o_ux) ((float *)o_ux)[k] = (float)ux;
+    if (o_uy) ((float *)o_uy)[k] = (float)uy;
+    if (o_T) ((float *)o_T)[k] = (float)t;
+  }
+}
+
+template <typename real>
+__global__ void export_populations(const Params<real> P, const real *f, double *out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.plane) return;
+  const NodeMap c = map_node(P, (int)(k % P.nx), (int)(k / P.nx));
+  const long long kc = (long long)c.y * P.nx + c.x;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const double w = q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    out[q * P.plane + k] = (double)f[q * P.plane + kc] + w * (double)P.rho_ref;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// kernel variants
+// ---------------------------------------------------------------------------------
+
+struct Variant {
+  int tx, ty, nt;
+  size_t smem;
+  const void *fn[2];  // [energy]
+};
+
+template <typename real, int TX, int TY, int NT>
+Variant make_variant() {
+  Variant v;
+  v.tx = TX;
+  v.ty = TY;
+  v.nt = NT;
+  v.smem = step_smem_bytes<real, TX, TY>();
+  v.fn[0] = (const void *)fused_step<real, false, TX, TY, NT>;
+  v.fn[1] = (const void *)fused_step<real, true, TX, TY, NT>;
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------------
+
+struct ppl_sim {
+  ppl_config cfg;  // boundary-array pointers re-pointed at the owned copies below
+  std::vector<double> h_rho_w[4], h_T_w[4];
+  std::vector<uint8_t> h_T_dir[4];
+  int prec = 0;
+  int nx = 0, ny = 0;
+  long long N = 0;
+  size_t rsz = 8;  // sizeof(real)
+  void *f[2] = {nullptr, nullptr};
+  void *T[2] = {nullptr, nullptr};
+  void *bnd = nullptr;  // device copies of the per-node boundary arrays
+  double *stats[2] = {nullptr, nullptr};
+  double *partials = nullptr;  // max(#step CTAs, 7 * #stats blocks)
+  double *norm_out = nullptr;  // 7 doubles
+  unsigned *counter = nullptr;
+  unsigned *status = nullptr;
+  double *upload = nullptr;  // 4 * N doubles staging for init / reset
+  int cur = 0;
+  int64_t step = 0;
+  int64_t launches = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [energy], captured from parity 0
+  Variant var;
+  dim3 grid;
+  int stats_blocks = 0;
+  Params<double> pd;
+  Params<float> pf;
+  uint64_t cfg_hash = 0;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return PPL_OK;
+  if (e == cudaErrorMemoryAllocation) return PPL_E_NOMEM;
+  return PPL_E_CUDA;
+}
+#define CK(x)                                   \
+  do {                                          \
+    int _rc = cuda_err(x);                      \
+    if (_rc != PPL_OK) return _rc;              \
+  } while (0)
+
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+  const unsigned char *c = (const unsigned char *)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t hash_config(const ppl_sim *h) {
+  const ppl_config &c = h->cfg;
+  uint64_t x = 1469598103934665603ull;
+  x = fnv(x, &c.nx, sizeof(c.nx));
+  x = fnv(x, &c.ny, sizeof(c.ny));
+  x = fnv(x, &c.precision, sizeof(c.precision));
+  const double sc[] = {c.rho_ref, c.a, c.b, c.R, c.omega, c.G, c.eta_l, c.eta_v, c.rho_l, c.rho_v,
+                       c.sigma, c.kappa, c.gx, c.gy, c.cv, c.lambda_l, c.lambda_v, c.G_w};
+  x = fnv(x, sc, sizeof(sc));
+  x = fnv(x, c.s, sizeof(c.s));
+  x = fnv(x, &c.energy_on, sizeof(c.energy_on));
+  x = fnv(x, &c.iso_steps, sizeof(c.iso_steps));
+  x = fnv(x, c.hydro_bc, sizeof(c.hydro_bc));
+  x = fnv(x, c.thermal_bc, sizeof(c.thermal_bc));
+  x = fnv(x, c.T_side, sizeof(c.T_side));
+  x = fnv(x, c.rho_w_side, sizeof(c.rho_w_side));
+  x = fnv(x, &c.contact_model, sizeof(c.contact_model));
+  for (int s = 0; s < 4; ++s) {
+    if (!h->h_rho_w[s].empty()) x = fnv(x, h->h_rho_w[s].data(), h->h_rho_w[s].size() * 8);
+    if (!h->h_T_w[s].empty()) x = fnv(x, h->h_T_w[s].data(), h->h_T_w[s].size() * 8);
+    if (!h->h_T_dir[s].empty()) x = fnv(x, h->h_T_dir[s].data(), h->h_T_dir[s].size());
+  }
+  return x;
+}
+
+int validate(const ppl_config *c) {
+  if (!c) return PPL_E_INVAL;
+  if (c->nx < 3 || c->ny < 3) return PPL_E_INVAL;
+  if ((long long)c->nx * c->ny > (1ll << 34)) return PPL_E_INVAL;
+  if (c->precision != PPL_FP64 && c->precision != PPL_FP32DEV) return PPL_E_INVAL;
+  if (!(c->a > 0) || !(c->b > 0) || !(c->R > 0) || !(c->G < 0)) return PPL_E_INVAL;
+  for (int i = 0; i < 9; ++i)
+    if (!(c->s[i] > 0 && c->s[i] < 2)) return PPL_E_INVAL;
+  if (!(c->rho_l != c->rho_v)) return PPL_E_INVAL;
+  if (c->contact_model != PPL_CONTACT_PSI) return PPL_E_INVAL;
+  if (c->energy_on && !(c->cv > 0)) return PPL_E_INVAL;
+  if (c->iso_steps < 0) return PPL_E_INVAL;
+  for (int s = 0; s < 4; ++s) {
+    if (c->hydro_bc[s] < 0 || c->hydro_bc[s] > 2) return PPL_E_INVAL;
+    if (c->thermal_bc[s] < 0 || c->thermal_bc[s] > 2) return PPL_E_INVAL;
+  }
+  int nonper_axes = 0;
+  for (int ax = 0; ax < 2; ++ax) {
+    const int s0 = 2 * ax, s1 = 2 * ax + 1;
+    const bool p0 = c->hydro_bc[s0] == PPL_PERIODIC, p1 = c->hydro_bc[s1] == PPL_PERIODIC;
+    if (p0 != p1) return PPL_E_INVAL;
+    const int len = ax == 0 ? c->nx : c->ny;
+    if (!p0) {
+      ++nonper_axes;
+      if (len < 4) return PPL_E_INVAL;
+      for (int s : {s0, s1})
+        if (c->thermal_bc[s] == PPL_T_PERIODIC && c->hydro_bc[s] == PPL_WALL) return PPL_E_INVAL;
+    } else {
+      // a periodic axis: temperature periodic, or Dirichlet rings on both sides
+      const bool t0 = c->thermal_bc[s0] == PPL_T_PERIODIC, t1 = c->thermal_bc[s1] == PPL_T_PERIODIC;
+      if (t0 != t1) return PPL_E_INVAL;
+      if (!t0 && (c->thermal_bc[s0] != PPL_T_DIRICHLET || c->thermal_bc[s1] != PPL_T_DIRICHLET))
+        return PPL_E_INVAL;
+      if (c->rho_w[s0] || c->rho_w[s1]) return PPL_E_INVAL;
+    }
+  }
+  if (nonper_axes > 1) return PPL_E_INVAL;
+  return PPL_OK;
+}
+
+template <typename real>
+void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real *const *tw,
+                 const uint8_t *const *td) {
+  const ppl_config &c = h->cfg;
+  memset(&P, 0, sizeof(P));
+  P.nx = c.nx;
+  P.ny = c.ny;
+  P.plane = (long long)c.nx * c.ny;
+  const double Tc = ppl_tc(c.a, c.b, c.R);
+  P.a = (real)c.a;
+  P.b = (real)c.b;
+  P.R = (real)c.R;
+  P.Tc = (real)Tc;
+  P.k = (real)(0.37464 + 1.54226 * c.omega - 0.2699 * c.omega * c.omega);
+  P.G = (real)c.G;
+  P.sqrt_Tc_inv = (real)(1.0 / std::sqrt(Tc));
+  for (int i = 0; i < 9; ++i) P.s[i] = (real)c.s[i];
+  P.var_eta = (c.eta_l > 0 && c.eta_v > 0) ? 1 : 0;
+  P.eta_l = (real)c.eta_l;
+  P.eta_v = (real)c.eta_v;
+  P.rho_l = (real)c.rho_l;
+  P.rho_v = (real)c.rho_v;
+  P.inv_drho = (real)(1.0 / (c.rho_l - c.rho_v));
+  // 12 sigma / (tau - 1/2) with tau = 1/s (Eq. S)
+  P.sigma12_e = (real)(12.0 * c.sigma / (1.0 / c.s[1] - 0.5));
+  P.sigma12_z = (real)(12.0 * c.sigma / (1.0 / c.s[2] - 0.5));
+  P.kappa_G2 = (real)(c.kappa * c.G / 2.0);
+  P.gx = (real)c.gx;
+  P.gy = (real)c.gy;
+  P.cv = (real)c.cv;
+  P.lam_l = (real)c.lambda_l;
+  P.lam_v = (real)c.lambda_v;
+  P.dlam = (real)((c.lambda_l - c.lambda_v) / (c.rho_l - c.rho_v));
+  for (int s = 0; s < 4; ++s) {
+    P.hbc[s] = c.hydro_bc[s];
+    P.tbc[s] = c.thermal_bc[s];
+    P.T_side[s] = (real)c.T_side[s];
+    P.rho_w_side[s] = (real)c.rho_w_side[s];
+    P.rho_w[s] = rw[s];
+    P.T_w[s] = tw[s];
+    P.T_dir[s] = td[s];
+  }
+  P.rho_ref = h->prec == PPL_FP32DEV ? (real)c.rho_ref : (real)0;
+  P.inv_nodes = 1.0 / (double)P.plane;
+}
+
+template <typename real>
+const Params<real> &params_of(const ppl_sim *h);
+template <>
+const Params<double> &params_of<double>(const ppl_sim *h) { return h->pd; }
+template <>
+const Params<float> &params_of<float>(const ppl_sim *h) { return h->pf; }
+
+template <typename real>
+int launch_step_t(ppl_sim *h, bool energy) {
+  const Params<real> &P = params_of<real>(h);
+  StepIO io;
+  io.f_in = h->f[h->cur];
+  io.T_in = h->T[h->cur];
+  io.f_out = h->f[1 - h->cur];
+  io.T_out = h->T[1 - h->cur];
+  io.stats_in = h->stats[h->cur];
+  io.stats_out = h->stats[1 - h->cur];
+  io.partials = h->partials;
+  io.counter = h->counter;
+  io.status = h->status;
+  void *args[] = {(void *)&P, (void *)&io};
+  CK(cudaLaunchKernel(h->var.fn[energy ? 1 : 0], h->grid, dim3(h->var.nt), args, h->var.smem, h->stream));
+  h->cur = 1 - h->cur;
+  h->step += 1;
+  h->launches += 1;
+  return PPL_OK;
+}
+
+int launch_step(ppl_sim *h, bool energy) {
+  return h->prec == PPL_FP64 ? launch_step_t<double>(h, energy) : launch_step_t<float>(h, energy);
+}
+
+bool energy_at(const ppl_sim *h, int64_t step) { return h->cfg.energy_on && step >= h->cfg.iso_steps; }
+
+int capture_graph(ppl_sim *h, int e) {
+  // capture kGraphSteps launches starting from parity 0; host bookkeeping is restored
+  const int cur0 = h->cur;
+  const int64_t step0 = h->step, l0 = h->launches;
+  h->cur = 0;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = PPL_OK;
+  for (int i = 0; i < kGraphSteps && rc == PPL_OK; ++i) rc = launch_step(h, e != 0);
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+  h->cur = cur0;
+  h->step = step0;
+  h->launches = l0;
+  if (rc != PPL_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(ce);
+  ce = cudaGraphInstantiate(&h->graph[e], g, 0);
+  cudaGraphDestroy(g);
+  CK(ce);
+  return PPL_OK;
+}
+
+template <typename real>
+int run_stats(ppl_sim *h, double *stats_dst) {
+  const Params<real> &P = params_of<real>(h);
+  stats_partials<real><<<h->stats_blocks, 256, 0, h->stream>>>(P, (const real *)h->f[h->cur],
+                                                               (const real *)h->T[h->cur], h->partials,
+                                                               h->status);
+  CK(cudaGetLastError());
+  stats_finalize<<<1, 32, 0, h->stream>>>(h->partials, h->stats_blocks, P.inv_nodes, h->norm_out, stats_dst);
+  CK(cudaGetLastError());
+  return PPL_OK;
+}
+
+int stats(ppl_sim *h, double *stats_dst) {
+  return h->prec == PPL_FP64 ? run_stats<double>(h, stats_dst) : run_stats<float>(h, stats_dst);
+}
+
+template <typename real>
+int upload_state_t(ppl_sim *h, const double *rho0, const double *ux0, const double *uy0, const double *T0) {
+  const size_t nb = (size_t)h->N * sizeof(double);
+  CK(cudaMemcpyAsync(h->upload, rho0, nb, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->upload + h->N, ux0, nb, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->upload + 2 * h->N, uy0, nb, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->upload + 3 * h->N, T0, nb, cudaMemcpyHostToDevice, h->stream));
+  const Params<real> &P = params_of<real>(h);
+  const int nt = 256;
+  const unsigned nb_blocks = (unsigned)((h->N + nt - 1) / nt);
+  init_state<real><<<nb_blocks, nt, 0, h->stream>>>(P, h->upload, h->upload + h->N, h->upload + 2 * h->N,
+                                                    h->upload + 3 * h->N, (real *)h->f[0], (real *)h->T[0]);
+  CK(cudaGetLastError());
+  return PPL_OK;
+}
+
+int upload_state(ppl_sim *h, const double *rho0, const double *ux0, const double *uy0, const double *T0) {
+  if (!rho0 || !ux0 || !uy0 || !T0) return PPL_E_INVAL;
+  h->cur = 0;
+  h->step = 0;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+  int rc = h->prec == PPL_FP64 ? upload_state_t<double>(h, rho0, ux0, uy0, T0)
+                               : upload_state_t<float>(h, rho0, ux0, uy0, T0);
+  if (rc) return rc;
+  rc = stats(h, h->stats[0]);
+  if (rc) return rc;
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st & (FLAG_PSI_NEG | FLAG_NAN | FLAG_RHO_NONPOS)) {
+    cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
+    cudaStreamSynchronize(h->stream);
+    return PPL_E_INVAL;
+  }
+  return PPL_OK;
+}
+
+int check_status(ppl_sim *h) {
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st ? PPL_E_NUMERIC : PPL_OK;
+}
+
+void free_all(ppl_sim *h) {
+  for (int e = 0; e < 2; ++e)
+    if (h->graph[e]) cudaGraphExecDestroy(h->graph[e]);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->f[i]);
+    cudaFree(h->T[i]);
+    cudaFree(h->stats[i]);
+  }
+  cudaFree(h->bnd);
+  cudaFree(h->partials);
+  cudaFree(h->norm_out);
+  cudaFree(h->counter);
+  cudaFree(h->status);
+  cudaFree(h->upload);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------
+
+extern "C" {
+
+const char *ppl_strerror(int code) {
+  switch (code) {
+    case PPL_OK: return "ok";
+    case PPL_E_INVAL: return "invalid argument, configuration or initial state";
+    case PPL_E_CUDA: return "CUDA runtime error";
+    case PPL_E_NUMERIC: return "numerical failure flagged on the device (NaN, rho <= 0 or negative psi argument)";
+    case PPL_E_TIMEOUT: return "bounded device wait timed out";
+    case PPL_E_IO: return "checkpoint I/O error or configuration mismatch";
+    case PPL_E_NOMEM: return "out of memory";
+    default: return "unknown error code";
+  }
+}
+
+double ppl_tc(double a, double b, double R) { return 0.0778 * a / (0.45724 * b * R); }
+
+double ppl_refine_a(double a_base, int32_t n_base, int32_t n) {
+  const double r = (double)n_base / (double)n;
+  return a_base * r * r;
+}
+
+// Maxwell equal-area rule for the PR isotherm (Sec. 3.2 target of the sigma tuning), using
+// the closed-form integral of p dv with v = 1/rho:
+//   int p dv = R T ln(v - b) - a alpha / (2 sqrt2 b) ln((v + b - sqrt2 b)/(v + b + sqrt2 b)).
+// Spinodal points and phase densities by bisection, p_sat by bisection on the area balance.
+int ppl_maxwell(double a, double b, double R, double omega, double T, double *rho_v, double *rho_l,
+                double *p_sat) {
+  if (!rho_v || !rho_l || !p_sat || !(a > 0) || !(b > 0) || !(R > 0) || !(T > 0)) return PPL_E_INVAL;
+  const double Tc = ppl_tc(a, b, R);
+  if (!(T < Tc)) return PPL_E_INVAL;
+  const double k = 0.37464 + 1.54226 * omega - 0.2699 * omega * omega;
+  const double ar = 1.0 + k * (1.0 - std::sqrt(T / Tc));
+  const double aa = a * ar * ar;
+  auto p = [&](double r) { return r * R * T / (1.0 - b * r) - aa * r * r / (1.0 + 2.0 * b * r - b * b * r * r); };
+  auto dp = [&](double r) {
+    const double d = 1.0 + 2.0 * b * r - b * b * r * r;
+    return R * T / ((1.0 - b * r) * (1.0 - b * r)) - aa * (2.0 * r * d - r * r * (2.0 * b - 2.0 * b * b * r)) / (d * d);
+  };
+  // bracket the spinodal: first sign change of dp/drho from + to - and back
+  const double rmax = 0.999999 / b;
+  const int n = 20000;
+  double ra = -1, rb = -1;
+  for (int i = 1; i < n; ++i) {
+    const double r0 = rmax * (i - 1) / n, r1 = rmax * i / n;
+    if (ra < 0 && dp(r0 + 1e-300) > 0 && dp(r1) <= 0) ra = r1;
+    if (ra > 0 && dp(r0) < 0 && dp(r1) >= 0) { rb = r1; break; }
+  }
+  if (ra < 0 || rb < 0) return PPL_E_INVAL;
+  auto bis = [&](auto fn, double lo, double hi) {
+    double flo = fn(lo);
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      const double fm = fn(mid);
+      if ((fm > 0) == (flo > 0)) { lo = mid; flo = fm; } else hi = mid;
+      if (hi - lo <= 1e-16 * hi) break;
+    }
+    return 0.5 * (lo + hi);
+  };
+  const double r_smax = bis(dp, ra - rmax / n, ra);  // local max of p
+  const double r_smin = bis(dp, rb - rmax / n, rb);  // local min of p
+  const double p_hi = p(r_smax), p_lo = std::fmax(p(r_smin), 1e-300);
+  const double s2 = std::sqrt(2.0);
+  auto prim = [&](double v) { return R * T * std::log(v - b) - aa / (2.0 * s2 * b) * std::log((v + b - s2 * b) / (v + b + s2 * b)); };
+  double rv = 0, rl = 0;
+  auto area = [&](double ps) {
+    rv = bis([&](double r) { return p(r) - ps; }, 1e-300, r_smax);
+    rl = bis([&](double r) { return p(r) - ps; }, r_smin, rmax);
+    const double vv = 1.0 / rv, vl = 1.0 / rl;
+    return prim(vv) - prim(vl) - ps * (vv - vl);
+  };
+  double lo = p_lo, hi = p_hi;
+  double alo = area(lo);
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double am = area(mid);
+    if ((am > 0) == (alo > 0)) { lo = mid; alo = am; } else hi = mid;
+    if (hi - lo <= 1e-16 * hi) break;
+  }
+  const double ps = 0.5 * (lo + hi);
+  area(ps);
+  *rho_v = rv;
+  *rho_l = rl;
+  *p_sat = ps;
+  return PPL_OK;
+}
+
+int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const double *uy0, const double *T0,
+             ppl_t **out) {
+  if (!out) return PPL_E_INVAL;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  ppl_sim *h = new (std::nothrow) ppl_sim();
+  if (!h) return PPL_E_NOMEM;
+  h->cfg = *cfg;
+  h->prec = cfg->precision;
+  h->nx = cfg->nx;
+  h->ny = cfg->ny;
+  h->N = (long long)cfg->nx * cfg->ny;
+  h->rsz = h->prec == PPL_FP64 ? 8 : 4;
+  for (int s = 0; s < 4; ++s) {
+    const int len = s < 2 ? cfg->ny : cfg->nx;
+    if (cfg->rho_w[s]) h->h_rho_w[s].assign(cfg->rho_w[s], cfg->rho_w[s] + len);
+    if (cfg->T_w[s]) h->h_T_w[s].assign(cfg->T_w[s], cfg->T_w[s] + len);
+    if (cfg->T_dirichlet[s]) h->h_T_dir[s].assign(cfg->T_dirichlet[s], cfg->T_dirichlet[s] + len);
+    h->cfg.rho_w[s] = h->h_rho_w[s].empty() ? nullptr : h->h_rho_w[s].data();
+    h->cfg.T_w[s] = h->h_T_w[s].empty() ? nullptr : h->h_T_w[s].data();
+    h->cfg.T_dirichlet[s] = h->h_T_dir[s].empty() ? nullptr : h->h_T_dir[s].data();
+  }
+  h->cfg_hash = hash_config(h);
+  auto fail = [&](int code) {
+    free_all(h);
+    delete h;
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PPL_E_CUDA);
+  h->stream = h->own_stream;
+
+  // kernel variant: the large tile unless the grid would give fewer than ~2 CTAs per SM
+  Variant big, small;
+  if (h->prec == PPL_FP64) {
+    big = make_variant<double, 32, 16, 256>();
+    small = make_variant<double, 16, 8, 128>();
+  } else {
+    big = make_variant<float, 64, 16, 256>();
+    small = make_variant<float, 32, 8, 128>();
+  }
+  const long long big_ctas = (long long)((h->nx + big.tx - 1) / big.tx) * ((h->ny + big.ty - 1) / big.ty);
+  h->var = big_ctas >= 304 ? big : small;
+  h->grid = dim3((h->nx + h->var.tx - 1) / h->var.tx, (h->ny + h->var.ty - 1) / h->var.ty);
+  for (int e = 0; e < 2; ++e)
+    if (cudaFuncSetAttribute(h->var.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->var.smem) !=
+        cudaSuccess)
+      return fail(PPL_E_CUDA);
+  h->stats_blocks = 608;
+  const size_t nctas = (size_t)h->grid.x * h->grid.y;
+  const size_t npart = nctas > (size_t)h->stats_blocks * 7 ? nctas : (size_t)h->stats_blocks * 7;
+
+  // device buffers
+  const size_t fbytes = (size_t)9 * h->N * h->rsz, tbytes = (size_t)h->N * h->rsz;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&h->f[i], fbytes) != cudaSuccess || cudaMalloc(&h->T[i], tbytes) != cudaSuccess ||
+        cudaMalloc(&h->stats[i], 2 * sizeof(double)) != cudaSuccess)
+      return fail(PPL_E_NOMEM);
+  }
+  if (cudaMalloc(&h->partials, npart * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->norm_out, 7 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&h->counter, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&h->status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&h->upload, (size_t)4 * h->N * sizeof(double)) != cudaSuccess)
+    return fail(PPL_E_NOMEM);
+  if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned), h->stream) != cudaSuccess) return fail(PPL_E_CUDA);
+
+  // boundary arrays in the working precision
+  size_t bbytes = 0;
+  for (int s = 0; s < 4; ++s) {
+    const size_t len = s < 2 ? h->ny : h->nx;
+    bbytes += (h->h_rho_w[s].empty() ? 0 : len * h->rsz) + (h->h_T_w[s].empty() ? 0 : len * h->rsz) +
+              (h->h_T_dir[s].empty() ? 0 : ((len + 15) / 16) * 16);
+  }
+  const void *rw[4] = {nullptr, nullptr, nullptr, nullptr}, *tw[4] = {nullptr, nullptr, nullptr, nullptr};
+  const uint8_t *td[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (bbytes) {
+    if (cudaMalloc(&h->bnd, bbytes) != cudaSuccess) return fail(PPL_E_NOMEM);
+    std::vector<unsigned char> host(bbytes);
+    size_t off = 0;
+    for (int s = 0; s < 4; ++s) {
+      const size_t len = s < 2 ? h->ny : h->nx;
+      auto put_real = [&](const std::vector<double> &v, const void **dst) {
+        if (v.empty()) return;
+        for (size_t i = 0; i < len; ++i) {
+          if (h->rsz == 8) memcpy(&host[off + i * 8], &v[i], 8);
+          else {
+            const float x = (float)v[i];
+            memcpy(&host[off + i * 4], &x, 4);
+          }
+        }
+        *dst = (const unsigned char *)h->bnd + off;
+        off += len * h->rsz;
+      };
+      put_real(h->h_rho_w[s], &rw[s]);
+      put_real(h->h_T_w[s], &tw[s]);
+      if (!h->h_T_dir[s].empty()) {
+        memcpy(&host[off], h->h_T_dir[s].data(), len);
+        td[s] = (const uint8_t *)h->bnd + off;
+        off += ((len + 15) / 16) * 16;
+      }
+    }
+    if (cudaMemcpy(h->bnd, host.data(), bbytes, cudaMemcpyHostToDevice) != cudaSuccess) return fail(PPL_E_CUDA);
+  }
+  if (h->prec == PPL_FP64)
+    fill_params<double>(h, h->pd, (const double *const *)rw, (const double *const *)tw, td);
+  else
+    fill_params<float>(h, h->pf, (const float *const *)rw, (const float *const *)tw, td);
+
+  rc = upload_state(h, rho0, ux0, uy0, T0);
+  if (rc) return fail(rc);
+  *out = h;
+  return PPL_OK;
+}
+
+int ppl_reset(ppl_t *h, const double *rho0, const double *ux0, const double *uy0, const double *T0) {
+  if (!h) return PPL_E_INVAL;
+  return upload_state(h, rho0, ux0, uy0, T0);
+}
+
+int ppl_set_stream(ppl_t *h, void *cuda_stream) {
+  if (!h) return PPL_E_INVAL;
+  h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+  return PPL_OK;
+}
+
+int ppl_step_async(ppl_t *h, int64_t nsteps) {
+  if (!h || nsteps < 0) return PPL_E_INVAL;
+  int64_t left = nsteps;
+  while (left > 0) {
+    const bool e = energy_at(h, h->step);
+    const bool uniform = energy_at(h, h->step + kGraphSteps - 1) == e;
+    if (h->cur == 0 && left >= kGraphSteps && uniform) {
+      if (!h->graph[e ? 1 : 0]) {
+        int rc = capture_graph(h, e ? 1 : 0);
+        if (rc) return rc;
+      }
+      CK(cudaGraphLaunch(h->graph[e ? 1 : 0], h->stream));
+      h->step += kGraphSteps;
+      h->launches += kGraphSteps;
+      left -= kGraphSteps;
+    } else {
+      int rc = launch_step(h, e);
+      if (rc) return rc;
+      left -= 1;
+    }
+  }
+  return PPL_OK;
+}
+
+int ppl_sync(ppl_t *h) {
+  if (!h) return PPL_E_INVAL;
+  return check_status(h);
+}
+
+int ppl_step(ppl_t *h, int64_t nsteps) {
+  int rc = ppl_step_async(h, nsteps);
+  if (rc) return rc;
+  return check_status(h);
+}
+
+int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtype) {
+  if (!h || (dtype != 0 && dtype != 1)) return PPL_E_INVAL;
+  const int nt = 256;
+  const unsigned nb = (unsigned)((h->N + nt - 1) / nt);
+  if (h->prec == PPL_FP64)
+    export_fields<double><<<nb, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur],
+                                                    (const double *)h->T[h->cur], h->stats[h->cur], rho, ux, uy,
+                                                    T, dtype);
+  else
+    export_fields<float><<<nb, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur],
+                                                   (const float *)h->T[h->cur], h->stats[h->cur], rho, ux, uy, T,
+                                                   dtype);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return PPL_OK;
+}
+
+int ppl_fields(ppl_t *h, double *rho, double *ux, double *uy, double *T) {
+  if (!h) return PPL_E_INVAL;
+  double *d = nullptr;
+  const size_t nb = (size_t)h->N * sizeof(double);
+  CK(cudaMalloc(&d, 4 * nb));
+  int rc = ppl_fields_device(h, rho ? d : nullptr, ux ? d + h->N : nullptr, uy ? d + 2 * h->N : nullptr,
+                             T ? d + 3 * h->N : nullptr, 0);
+  double *dst[4] = {rho, ux, uy, T};
+  for (int i = 0; i < 4 && rc == PPL_OK; ++i)
+    if (dst[i]) rc = cuda_err(cudaMemcpyAsync(dst[i], d + i * h->N, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
+  cudaFree(d);
+  return rc;
+}
+
+int ppl_populations(ppl_t *h, double *f) {
+  if (!h || !f) return PPL_E_INVAL;
+  double *d = nullptr;
+  const size_t nb = (size_t)9 * h->N * sizeof(double);
+  CK(cudaMalloc(&d, nb));
+  const int nt = 256;
+  const unsigned blocks = (unsigned)((h->N + nt - 1) / nt);
+  if (h->prec == PPL_FP64)
+    export_populations<double><<<blocks, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], d);
+  else
+    export_populations<float><<<blocks, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], d);
+  int rc = cuda_err(cudaGetLastError());
+  if (rc == PPL_OK) rc = cuda_err(cudaMemcpyAsync(f, d, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
+  cudaFree(d);
+  return rc;
+}
+
+int ppl_norms(ppl_t *h, ppl_norms_t *out) {
+  if (!h || !out) return PPL_E_INVAL;
+  int rc = stats(h, nullptr);
+  if (rc) return rc;
+  double v[7];
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(v, h->norm_out, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out->step = h->step;
+  out->mass = v[0];
+  out->rho_mean = v[0] / (double)h->N;
+  out->sum_abs_rho = v[1];
+  out->sum_abs_T = v[2];
+  out->rho_min = v[3];
+  out->rho_max = v[4];
+  out->T_min = v[5];
+  out->T_max = v[6];
+  out->flags = st;
+  return PPL_OK;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nx, ny, precision, rsz, pad;
+  int64_t step;
+  uint64_t cfg_hash;
+};
+
+int ppl_save(ppl_t *h, const char *path) {
+  if (!h || !path) return PPL_E_INVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  const size_t fbytes = (size_t)9 * h->N * h->rsz, tbytes = (size_t)h->N * h->rsz;
+  std::vector<unsigned char> buf(fbytes + tbytes);
+  double st[2];
+  CK(cudaMemcpy(buf.data(), h->f[h->cur], fbytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(buf.data() + fbytes, h->T[h->cur], tbytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st, h->stats[h->cur], sizeof(st), cudaMemcpyDeviceToHost));
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "PPLCKPT1", 8);
+  hd.version = 1;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.precision = h->prec;
+  hd.rsz = (int32_t)h->rsz;
+  hd.step = h->step;
+  hd.cfg_hash = h->cfg_hash;
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return PPL_E_IO;
+  bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(st, sizeof(st), 1, fp) == 1 &&
+            fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? PPL_OK : PPL_E_IO;
+}
+
+int ppl_load(ppl_t *h, const char *path) {
+  if (!h || !path) return PPL_E_INVAL;
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return PPL_E_IO;
+  CkptHeader hd;
+  double st[2];
+  const size_t fbytes = (size_t)9 * h->N * h->rsz, tbytes = (size_t)h->N * h->rsz;
+  std::vector<unsigned char> buf(fbytes + tbytes);
+  bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "PPLCKPT1", 8) == 0 && hd.version == 1 &&
+            hd.nx == h->nx && hd.ny == h->ny && hd.precision == h->prec && hd.rsz == (int32_t)h->rsz &&
+            hd.cfg_hash == h->cfg_hash && fread(st, sizeof(st), 1, fp) == 1 &&
+            fread(buf.data(), 1, buf.size(), fp) == buf.size();
+  fclose(fp);
+  if (!ok) return PPL_E_IO;
+  CK(cudaStreamSynchronize(h->stream));
+  h->cur = 0;
+  CK(cudaMemcpy(h->f[0], buf.data(), fbytes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->T[0], buf.data() + fbytes, tbytes, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->stats[0], st, sizeof(st), cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->status, 0, sizeof(unsigned)));
+  h->step = hd.step;
+  return PPL_OK;
+}
+
+int64_t ppl_launch_count(const ppl_t *h) { return h ? h->launches : -1; }
+
+void ppl_destroy(ppl_t *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+"""ctypes binding of libppl (include/ppl.h): argument marshalling only.
+
+Every step of the time integration runs in the sm_103a kernels of libppl.so. There is
+no CPU fallback: if the library is missing or no CUDA device is present the calls
+raise. PyTorch, when used, only supplies device buffers and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PPL_OK, PPL_E_INVAL, PPL_E_CUDA, PPL_E_NUMERIC, PPL_E_TIMEOUT, PPL_E_IO, PPL_E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+PPL_FP64, PPL_FP32DEV = 0, 1
+FLAG_PSI_NEG, FLAG_NAN, FLAG_RHO_NONPOS = 1, 2, 4
+
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PU8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+class PplConfig(ctypes.Structure):
+    """Mirror of ppl_config in include/ppl.h."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("rho_ref", _D), ("a", _D), ("b", _D), ("R", _D), ("omega", _D), ("G", _D),
+        ("s", _D * 9),
+        ("eta_l", _D), ("eta_v", _D), ("rho_l", _D), ("rho_v", _D),
+        ("sigma", _D), ("kappa", _D), ("gx", _D), ("gy", _D), ("cv", _D), ("lambda_l", _D), ("lambda_v", _D),
+        ("energy_on", ctypes.c_int32), ("iso_steps", ctypes.c_int64),
+        ("hydro_bc", ctypes.c_int32 * 4), ("thermal_bc", ctypes.c_int32 * 4),
+        ("T_side", _D * 4), ("rho_w_side", _D * 4),
+        ("rho_w", _PD * 4), ("T_w", _PD * 4), ("T_dirichlet", _PU8 * 4),
+        ("contact_model", ctypes.c_int32), ("G_w", _D),
+    ]
+
+
+class PplNorms(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("mass", _D), ("rho_mean", _D), ("sum_abs_rho", _D),
+                ("sum_abs_T", _D), ("rho_min", _D), ("rho_max", _D), ("T_min", _D), ("T_max", _D),
+                ("flags", ctypes.c_uint32)]
+
+
+class PplError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = load_library().ppl_strerror(code).decode()
+        super().__init__("%s: %s (code %d)" % (what, msg, code))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libppl.so (building it in-tree with nvcc when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build_library()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libppl.so is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(_build.LIB)
+    H = ctypes.c_void_p
+    L.ppl_init.argtypes = [ctypes.POINTER(PplConfig), _PD, _PD, _PD, _PD, ctypes.POINTER(H)]
+    L.ppl_reset.argtypes = [H, _PD, _PD, _PD, _PD]
+    L.ppl_set_stream.argtypes = [H, ctypes.c_void_p]
+    L.ppl_step.argtypes = [H, ctypes.c_int64]
+    L.ppl_step_async.argtypes = [H, ctypes.c_int64]
+    L.ppl_sync.argtypes = [H]
+    L.ppl_fields.argtypes = [H, _PD, _PD, _PD, _PD]
+    L.ppl_fields_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int]
+    L.ppl_populations.argtypes = [H, _PD]
+    L.ppl_norms.argtypes = [H, ctypes.POINTER(PplNorms)]
+    L.ppl_save.argtypes = [H, ctypes.c_char_p]
+    L.ppl_load.argtypes = [H, ctypes.c_char_p]
+    L.ppl_launch_count.argtypes = [H]
+    L.ppl_launch_count.restype = ctypes.c_int64
+    L.ppl_destroy.argtypes = [H]
+    L.ppl_destroy.restype = None
+    L.ppl_strerror.argtypes = [ctypes.c_int]
+    L.ppl_strerror.restype = ctypes.c_char_p
+    L.ppl_tc.argtypes = [_D, _D, _D]
+    L.ppl_tc.restype = _D
+    L.ppl_maxwell.argtypes = [_D, _D, _D, _D, _D, _PD, _PD, _PD]
+    L.ppl_refine_a.argtypes = [_D, ctypes.c_int32, ctypes.c_int32]
+    L.ppl_refine_a.restype = _D
+    for name in ("ppl_init", "ppl_reset", "ppl_set_stream", "ppl_step", "ppl_step_async", "ppl_sync",
+                 "ppl_fields", "ppl_fields_device", "ppl_populations", "ppl_norms", "ppl_save", "ppl_load",
+                 "ppl_maxwell"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != PPL_OK:
+        raise PplError(rc, what)
+
+
+def tc(a: float, b: float, R: float = 1.0) -> float:
+    """Critical temperature of the PR EOS (ppl_tc)."""
+    return load_library().ppl_tc(a, b, R)
+
+
+def maxwell(a: float, b: float, R: float, omega: float, T: float):
+    """Maxwell coexistence (rho_v, rho_l, p_sat) of the PR isotherm (ppl_maxwell)."""
+    rv, rl, ps = _D(), _D(), _D()
+    _check(load_library().ppl_maxwell(a, b, R, omega, T, ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps)),
+           "ppl_maxwell")
+    return rv.value, rl.value, ps.value
+
+
+def refine_a(a_base: float, n_base: int, n: int) -> float:
+    return load_library().ppl_refine_a(a_base, n_base, n)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_PD)
+
+
+def make_config(cfg: dict):
+    """Marshal a config dict (schema of the workloads module) into ppl_config."""
+    C = PplConfig()
+    keep = []
+    C.nx, C.ny = int(cfg["nx"]), int(cfg["ny"])
+    prec = cfg.get("precision", "fp64")
+    C.precision = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV}[prec] if isinstance(prec, str) else int(prec)
+    C.rho_ref = float(cfg.get("rho_ref", 1.0))
+    for k in ("a", "b", "R", "omega", "G", "eta_l", "eta_v", "rho_l", "rho_v", "sigma", "kappa", "gx", "gy",
+              "cv", "lambda_l", "lambda_v"):
+        setattr(C, k, float(cfg[k]))
+    for i in range(9):
+        C.s[i] = float(cfg["s"][i])
+    C.energy_on = int(cfg["energy_on"])
+    C.iso_steps = int(cfg["iso_steps"])
+    for sd in range(4):
+        C.hydro_bc[sd] = int(cfg["hydro_bc"][sd])
+        C.thermal_bc[sd] = int(cfg["thermal_bc"][sd])
+        C.T_side[sd] = float(cfg["T_side"][sd])
+        C.rho_w_side[sd] = float(cfg["rho_w_side"][sd])
+        for name, dt, ptr in (("rho_w", np.float64, _PD), ("T_w", np.float64, _PD), ("T_dirichlet", np.uint8, _PU8)):
+            arr = (cfg.get(name) or [None] * 4)[sd]
+            if arr is None:
+                getattr(C, name)[sd] = ctypes.cast(None, ptr)
+            else:
+                a = np.ascontiguousarray(arr, dtype=dt)
+                keep.append(a)
+                getattr(C, name)[sd] = a.ctypes.data_as(ptr)
+    C.contact_model = 0
+    C.G_w = float(cfg.get("G_w", 0.0))
+    return C, keep
+
+
+class Simulation:
+    """One ppl handle: device-resident state advanced by the fused sm_103a step kernel."""
+
+    def __init__(self, cfg: dict, rho0, ux0, uy0, T0, stream=None):
+        self.lib = load_library()
+        self.cfg = dict(cfg)
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self._c, self._keep = make_config(cfg)
+        self.h = ctypes.c_void_p()
+        arrs = self._host_fields(rho0, ux0, uy0, T0)
+        _check(self.lib.ppl_init(ctypes.byref(self._c), *[_ptr(a) for a in arrs], ctypes.byref(self.h)), "ppl_init")
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _host_fields(self, *fields):
+        return [np.ascontiguousarray(v, dtype=np.float64).reshape(self.ny, self.nx) for v in fields]
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (library stream)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(self.lib.ppl_set_stream(self.h, ctypes.c_void_p(handle or None)), "ppl_set_stream")
+
+    def reset(self, rho0, ux0, uy0, T0):
+        arrs = self._host_fields(rho0, ux0, uy0, T0)
+        _check(self.lib.ppl_reset(self.h, *[_ptr(a) for a in arrs]), "ppl_reset")
+
+    def step(self, n: int = 1):
+        _check(self.lib.ppl_step(self.h, int(n)), "ppl_step")
+
+    def step_async(self, n: int = 1):
+        _check(self.lib.ppl_step_async(self.h, int(n)), "ppl_step_async")
+
+    def sync(self):
+        _check(self.lib.ppl_sync(self.h), "ppl_sync")
+
+    def fields(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(self.lib.ppl_fields(self.h, *[_ptr(a) for a in out]), "ppl_fields")
+        return dict(zip(("rho", "ux", "uy", "T"), out))
+
+    def fields_device(self, torch_dtype=None):
+        import torch
+        dt = torch_dtype or torch.float64
+        code = {torch.float64: 0, torch.float32: 1}[dt]
+        out = [torch.empty((self.ny, self.nx), dtype=dt, device="cuda") for _ in range(4)]
+        _check(self.lib.ppl_fields_device(self.h, *[ctypes.c_void_p(t.data_ptr()) for t in out], code),
+               "ppl_fields_device")
+        return dict(zip(("rho", "ux", "uy", "T"), out))
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        _check(self.lib.ppl_populations(self.h, _ptr(f)), "ppl_populations")
+        return f
+
+    def norms(self):
+        n = PplNorms()
+        _check(self.lib.ppl_norms(self.h, ctypes.byref(n)), "ppl_norms")
+        return {k: getattr(n, k) for k, _ in PplNorms._fields_}
+
+    def save(self, path: str):
+        _check(self.lib.ppl_save(self.h, os.fsencode(path)), "ppl_save")
+
+    def load(self, path: str):
+        _check(self.lib.ppl_load(self.h, os.fsencode(path)), "ppl_load")
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.ppl_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.ppl_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,159 @@
+"""GPU parity: the sm_103a fused step through the C ABI against the CPU FP64 oracle,
+element by element on the same seeded inputs (populations, rho, u and T)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle, thermo
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-10  # spec bound for the FP64 path (relative, rho and T)
+
+
+@pytest.fixture(scope="module")
+def sim_cls():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04560_gb300 import Simulation
+    return Simulation
+
+
+@pytest.fixture(scope="module")
+def th():
+    e = thermo.PR()
+    out = {"e": e}
+    for tr in (0.8, 0.86):
+        out[tr] = thermo.maxwell(e, tr * e.Tc)
+    out["sigma086"] = thermo.sigma_for(e, 0.86 * e.Tc)
+    return out
+
+
+def run_pair(Sim, cfg, ic, steps):
+    sim = Sim(cfg, *ic)
+    sim.step(steps)
+    got = sim.fields()
+    got["f"] = sim.populations()
+    got["norms"] = sim.norms()
+    got["launches"] = sim.launch_count
+    sim.close()
+    ref = oracle.Oracle(cfg, *ic)
+    ref.step(steps)
+    want = ref.fields()
+    want["f"] = ref.f
+    return got, want
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
+
+
+def assert_fp64_parity(got, want, u_atol=1e-12):
+    assert rel(got["rho"], want["rho"]) <= FP64_RTOL
+    assert rel(got["T"], want["T"]) <= FP64_RTOL
+    np.testing.assert_allclose(got["f"], want["f"], rtol=FP64_RTOL, atol=1e-13)
+    np.testing.assert_allclose(got["ux"], want["ux"], rtol=0, atol=u_atol)
+    np.testing.assert_allclose(got["uy"], want["uy"], rtol=0, atol=u_atol)
+
+
+def test_static_droplet_fp64_5000_steps(sim_cls, th):
+    # isothermal static droplet, 64x64 periodic, 5,000 steps (the spec case)
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=64, R0=16.0, width=3.0)
+    got, want = run_pair(sim_cls, cfg, ic, 5000)
+    assert_fp64_parity(got, want)
+    assert got["launches"] == 5000
+    assert got["norms"]["flags"] == 0
+    m0 = ic[0].sum()  # f^eq initial state has exactly this mass up to rounding
+    assert abs(got["norms"]["mass"] - want["rho"].sum()) < 1e-12 * m0
+
+
+def test_ragged_droplet_all_source_terms_fp64(sim_cls, th):
+    # ragged tiles in both axes, kappa, gravity, variable eta, unequal rates
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=70, ny=45, R0=11.0, kappa=0.3)
+    cfg.update(gx=2e-5, gy=-4e-5, eta_l=0.1, eta_v=0.05, s=[1.0, 0.8, 0.9, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25])
+    got, want = run_pair(sim_cls, cfg, ic, 400)
+    assert_fp64_parity(got, want)
+
+
+def test_stefan_strip_walls_outflow_energy_fp64(sim_cls, th):
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=5, n_vapour=10)
+    got, want = run_pair(sim_cls, cfg, ic, 1500)
+    assert_fp64_parity(got, want)
+
+
+def test_pool_boiling_small_fp64(sim_cls, th):
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=100, ny=83, g=3e-5)
+    got, want = run_pair(sim_cls, cfg, ic, 300)
+    assert_fp64_parity(got, want)
+
+
+def test_droplet_vaporization_dirichlet_ring_fp64(sim_cls, th):
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.droplet_vaporization(e.Tc, rv, rl, 0.1, nx=60, ny=52, R0=12.0, iso_steps=40)
+    got, want = run_pair(sim_cls, cfg, ic, 240)
+    assert_fp64_parity(got, want)
+
+
+@pytest.mark.parametrize("prec,nx,ny", [("fp64", 610, 250), ("fp32", 1222, 250)])
+def test_large_tile_variant_pool_boiling(sim_cls, th, prec, nx, ny):
+    # grids large enough to select the big-tile kernel (>= 304 CTAs), ragged in x and y
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=nx, ny=ny, g=3e-5, precision=prec)
+    steps = 12
+    got, want = run_pair(sim_cls, cfg, ic, steps)
+    if prec == "fp64":
+        assert_fp64_parity(got, want)
+    else:
+        assert rel(got["rho"], want["rho"]) <= 1e-4
+        assert rel(got["T"], want["T"]) <= 1e-4
+
+
+def test_fp32_deviation_storage_error_budget(sim_cls, th):
+    # FP32 arithmetic with f_i - w_i rho_ref storage: within 1e-4 relative of the FP64
+    # oracle in rho and T on the Stefan strip
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=5, n_vapour=10, precision="fp32")
+    got, want = run_pair(sim_cls, cfg, ic, 1500)
+    assert rel(got["rho"], want["rho"]) <= 1e-4
+    assert rel(got["T"], want["T"]) <= 1e-4
+
+
+def test_checkpoint_resume_is_bit_identical(sim_cls, th, tmp_path):
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=64, ny=72, g=3e-5)
+    a = sim_cls(cfg, *ic)
+    a.step(70)
+    a.save(str(tmp_path / "ck.bin"))
+    a.step(50)
+    fa = a.populations()
+    b = sim_cls(cfg, *ic)
+    b.load(str(tmp_path / "ck.bin"))
+    b.step(50)
+    np.testing.assert_array_equal(b.populations(), fa)
+    np.testing.assert_array_equal(b.fields()["T"], a.fields()["T"])
+    a.close()
+    b.close()
+
+
+def test_invalid_initial_state_is_rejected(sim_cls):
+    from paper_2201_04560_gb300 import PplError
+    e = thermo.PR()
+    cfg = W.base_config(16, 16)
+    rho = np.full((16, 16), 9.0)
+    z = np.zeros((16, 16))
+    with pytest.raises(PplError) as ei:
+        sim_cls(cfg, rho, z, z, np.full((16, 16), 2.0 * e.Tc))
+    assert ei.value.code == -1

@@ -111,13 +111,18 @@ def stefan_strip(Tc, rho_v, rho_l, sigma, nx=1024, ny=4, n_vapour=10, dT_ratio=0
 
 
 def droplet_vaporization(Tc, rho_v, rho_l, sigma, nx=256, ny=256, R0=40.0, width=3.0, T_ratio=0.8,
-                         Tv_ratio=0.9, kappa=0.3, iso_steps=10000, precision="fp64"):
+                         Tv_ratio=0.9, kappa=0.3, iso_steps=10000, lam=0.25, precision="fp64"):
     """Droplet in superheated vapour (Sec. 4.1): periodic hydrodynamics, temperature held
-    at T_v on the boundary ring, isothermal for the first iso_steps."""
+    at T_v on the boundary ring, isothermal for the first iso_steps.
+
+    lam: conductivity of both phases. The paper's 2/3 gives a vapour diffusivity
+    lambda/(rho_v c_v) = 0.35 at T_sat = 0.86 Tc, inside the explicit Heun limit
+    alpha <= 3/8 of the lattice Laplacian; at 0.8 Tc (rho_v = 0.197) it would be 0.68
+    and the FD step would be unstable, hence the smaller default."""
     T_l, T_v = T_ratio * Tc, Tv_ratio * Tc
     cfg = base_config(
         nx, ny, s=[1.25] * 9, eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v, sigma=sigma,
-        kappa=kappa, cv=5.0, lambda_l=2.0 / 3.0, lambda_v=2.0 / 3.0, energy_on=1, iso_steps=iso_steps,
+        kappa=kappa, cv=5.0, lambda_l=lam, lambda_v=lam, energy_on=1, iso_steps=iso_steps,
         thermal_bc=[T_DIRICHLET] * 4, T_side=[T_v] * 4, precision=precision, rho_ref=rho_v)
     return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T_l, T_v)
 
