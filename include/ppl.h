@@ -50,7 +50,7 @@ extern "C" {
 
 /* ---- enumerations ---- */
 #define PPL_FP64 0    /* populations and arithmetic in FP64 */
-#define PPL_FP32DEV 1 /* FP32 arithmetic; populations stored as f_i - w_i rho_ref in FP32 */
+#define PPL_FP32DEV 1 /* FP32 arithmetic; f_i - w_i rho_ref and T - T_ref stored in FP32 */
 
 #define PPL_PERIODIC 0 /* hydrodynamic side kinds */
 #define PPL_WALL 1     /* Zou-He no-slip wet node + psi-based adhesion (Sec. 2.2) */
@@ -72,6 +72,7 @@ extern "C" {
  *  nx, ny        grid size (nx, ny >= 3; a non-periodic axis needs >= 4 nodes)
  *  precision     PPL_FP64 or PPL_FP32DEV
  *  rho_ref       reference density of the FP32 deviation storage (ignored for FP64)
+ *  T_ref         reference temperature: FP32 stores T - T_ref (ignored for FP64)
  *  a, b, R, omega  Peng-Robinson EOS (Eq. peng-robinson); T_c = 0.0778 a / (0.45724 b R)
  *  G             pseudopotential strength of Eq. (psi), must be < 0 (the paper uses -1)
  *  s[9]          diagonal of Lambda in the row order of M: s_rho, s_e, s_zeta, s_j, s_q, s_j, s_q, s_eta, s_eta
@@ -94,6 +95,7 @@ typedef struct ppl_config {
   int32_t nx, ny;
   int32_t precision;
   double rho_ref;
+  double T_ref;
   double a, b, R, omega, G;
   double s[9];
   double eta_l, eta_v, rho_l, rho_v;

@@ -42,7 +42,8 @@ __global__ void init_state(const Params<real> P, const double *rho0, const doubl
     f[q * P.plane + k] = (real)(fe - w * rr);
   }
   real tv;
-  T[k] = t_fixed(P, gx, gy, &tv) ? tv : (real)T0[k];
+  const double Tabs = t_fixed(P, gx, gy, &tv) ? (double)tv : T0[k];
+  T[k] = (real)(Tabs - (double)P.T_ref);
 }
 
 // Per-node diagnostics of the stored state, reduced per block into 7 FP64 partials:
@@ -63,7 +64,7 @@ __global__ void stats_partials(const Params<real> P, const real *f, const real *
 #pragma unroll
     for (int q = 0; q < 9; ++q) d += f[q * P.plane + k];
     const real rho = P.rho_ref + d;
-    const real t = T[k];
+    const real t = P.T_ref + T[k];
     const real arg = psi_arg(P, rho, t);
     if (!(arg >= real(0))) flags |= FLAG_PSI_NEG;
     const int ws = wall_side(P, gx, gy);
@@ -139,7 +140,7 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
 #pragma unroll
   for (int q = 0; q < 9; ++q) d += fl[q];
   const real rho = P.rho_ref + d;
-  const real t = T[kc];
+  const real t = P.T_ref + T[kc];
   const real jx = fl[1] - fl[3] + fl[5] - fl[6] - fl[7] + fl[8];
   const real jy = fl[2] - fl[4] + fl[5] + fl[6] - fl[7] - fl[8];
   const real psi_c = sqrt(fmax(psi_arg(P, rho, t), real(0)));
@@ -156,7 +157,7 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
       const long long kn = (long long)m.y * P.nx + m.x;
       real dn = 0;
       for (int r = 0; r < 9; ++r) dn += f[r * P.plane + kn];
-      pn = sqrt(fmax(psi_arg(P, P.rho_ref + dn, T[kn]), real(0)));
+      pn = sqrt(fmax(psi_arg(P, P.rho_ref + dn, P.T_ref + T[kn]), real(0)));
     }
     const real w = q < 5 ? real(1) / real(3) : real(1) / real(12);
     sx += w * pn * real(kCX[q]);
@@ -279,7 +280,7 @@ uint64_t hash_config(const ppl_sim *h) {
   x = fnv(x, &c.nx, sizeof(c.nx));
   x = fnv(x, &c.ny, sizeof(c.ny));
   x = fnv(x, &c.precision, sizeof(c.precision));
-  const double sc[] = {c.rho_ref, c.a, c.b, c.R, c.omega, c.G, c.eta_l, c.eta_v, c.rho_l, c.rho_v,
+  const double sc[] = {c.rho_ref, c.T_ref, c.a, c.b, c.R, c.omega, c.G, c.eta_l, c.eta_v, c.rho_l, c.rho_v,
                        c.sigma, c.kappa, c.gx, c.gy, c.cv, c.lambda_l, c.lambda_v, c.G_w};
   x = fnv(x, sc, sizeof(sc));
   x = fnv(x, c.s, sizeof(c.s));
@@ -381,6 +382,7 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
     P.T_dir[s] = td[s];
   }
   P.rho_ref = h->prec == PPL_FP32DEV ? (real)c.rho_ref : (real)0;
+  P.T_ref = h->prec == PPL_FP32DEV ? (real)c.T_ref : (real)0;
   P.inv_nodes = 1.0 / (double)P.plane;
 }
 

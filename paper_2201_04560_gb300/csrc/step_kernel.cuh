@@ -16,9 +16,11 @@
 //            by the last CTA into rho_bar for the next launch.
 // The halo recompute keeps DRAM traffic at one read and one write of (f, T) per node.
 //
-// Populations are stored as deviations f~_i = f_i - w_i rho_ref (rho_ref = 0 for the FP64
-// path, so both precisions share one arithmetic): the moments carry rho_ref only in
-// m_0, m_1, m_2, which the collision handles explicitly.
+// Populations are stored as deviations f~_i = f_i - w_i rho_ref and the temperature as
+// T - T_ref (rho_ref = T_ref = 0 for the FP64 path, so both precisions share one
+// arithmetic): the moments carry rho_ref only in m_0, m_1, m_2, which the collision
+// handles explicitly; the FD stencils act on the deviation directly and only the EOS
+// and the compression term use T_ref + (T - T_ref).
 #pragma once
 
 #include <cstdint>
@@ -47,6 +49,7 @@ struct Params {
   const real *T_w[4];
   const uint8_t *T_dir[4];
   real rho_ref;
+  real T_ref;        // T is stored as T - T_ref (0 for the FP64 path)
   double inv_nodes;  // 1 / (nx ny)
 };
 
@@ -304,8 +307,8 @@ __device__ __forceinline__ void collide(const Params<real> &P, real fd[9], real 
 }
 
 // ---- FD operator of Eq. (energy-equation) with lattice-weight stencils ----
-// th: temperature field with row stride WT, centre index it; rho/ux/uy: coefficient
-// fields (frozen at time n) with row stride W3, centre index i3.
+// th: temperature deviation T - T_ref with row stride WT, centre index it; rho/ux/uy:
+// coefficient fields (frozen at time n) with row stride W3, centre index i3.
 template <typename real, int WT, int W3>
 __device__ __forceinline__ real energy_L(const Params<real> &P, const real *th, int it, const real *rho,
                                          const real *ux, const real *uy, int i3) {
@@ -328,8 +331,9 @@ __device__ __forceinline__ real energy_L(const Params<real> &P, const real *th, 
                    twelfth * (uy[i3 + W3 + 1] + uy[i3 + W3 - 1] - uy[i3 - W3 - 1] - uy[i3 - W3 + 1]);
   const real lam = P.lam_v + P.dlam * (r0 - P.rho_v);
   const real inv_rcv = real(1) / (r0 * P.cv);
+  const real t_abs = P.T_ref + t0;
   return -(ux[i3] * gtx + uy[i3] * gty) + (lam * lap + P.dlam * (grx * gtx + gry * gty)) * inv_rcv -
-         t0 * dp_dT(P, r0, t0) * div * inv_rcv;
+         t_abs * dp_dT(P, r0, t_abs) * div * inv_rcv;
 }
 
 template <typename real>
@@ -377,14 +381,14 @@ __global__ void __launch_bounds__(NT) fused_step(const Params<real> P, const Ste
     for (int q = 0; q < 9; ++q) f[q] = ld_real<real>(io.f_in, q * plane + k);
     const real delta = ((f[0] + (f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
     const real rho = P.rho_ref + delta;
-    const real T = ld_real<real>(io.T_in, k);
+    const real T = ld_real<real>(io.T_in, k);  // T - T_ref
     s_rho[i] = rho;
     s_T[i] = T;
     s_jx[i] = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
     s_jy[i] = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     real psi = real(0);
     if (!m.solid) {
-      const real arg = psi_arg(P, rho, T);
+      const real arg = psi_arg(P, rho, P.T_ref + T);
       if (!(arg >= real(0))) flags |= FLAG_PSI_NEG;
       psi = sqrt(fmax(arg, real(0)));
     }
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(NT) fused_step(const Params<real> P, const Ste
       sx = (p1 - p3) / real(3) + (p5 - p6 - p7 + p8) / real(12);
       sy = (p2 - p4) / real(3) + (p5 + p6 - p7 - p8) / real(12);
     } else {
-      const real argw = psi_arg(P, wall_rho_w(P, ws, mm.x, mm.y), s_T[i]);
+      const real argw = psi_arg(P, wall_rho_w(P, ws, mm.x, mm.y), P.T_ref + s_T[i]);
       if (!(argw >= real(0))) flags |= FLAG_PSI_NEG;
       const real psi_w = sqrt(fmax(argw, real(0)));
       sx = real(0);
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(NT) fused_step(const Params<real> P, const Ste
 #pragma unroll
         for (int q = 1; q < 9; ++q) pn[q] = s_psi[i + kCY[q] * W3 + kCX[q]];
       } else {
-        const real psi_w = sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, m.x, m.y), s_T[i]), real(0)));
+        const real psi_w = sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, m.x, m.y), P.T_ref + s_T[i]), real(0)));
 #pragma unroll
         for (int q = 1; q < 9; ++q)
           pn[q] = beyond_wall(P, gx + kCX[q], gy + kCY[q]) ? psi_w : s_psi[i + kCY[q] * W3 + kCX[q]];
@@ -505,7 +509,7 @@ __global__ void __launch_bounds__(NT) fused_step(const Params<real> P, const Ste
       real Tw;
       real k1 = real(0), Ts;
       if (t_fixed(P, m.x, m.y, &Tw)) {
-        Ts = Tw;
+        Ts = Tw - P.T_ref;
       } else {
         k1 = energy_L<real, W3, W3>(P, s_T, i, s_rho, s_ux, s_uy, i);
         Ts = s_T[i] + k1;

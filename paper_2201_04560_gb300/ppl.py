@@ -27,7 +27,7 @@ class PplConfig(ctypes.Structure):
 
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("rho_ref", _D), ("a", _D), ("b", _D), ("R", _D), ("omega", _D), ("G", _D),
+        ("rho_ref", _D), ("T_ref", _D), ("a", _D), ("b", _D), ("R", _D), ("omega", _D), ("G", _D),
         ("s", _D * 9),
         ("eta_l", _D), ("eta_v", _D), ("rho_l", _D), ("rho_v", _D),
         ("sigma", _D), ("kappa", _D), ("gx", _D), ("gy", _D), ("cv", _D), ("lambda_l", _D), ("lambda_v", _D),
@@ -136,6 +136,7 @@ def make_config(cfg: dict):
     prec = cfg.get("precision", "fp64")
     C.precision = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV}[prec] if isinstance(prec, str) else int(prec)
     C.rho_ref = float(cfg.get("rho_ref", 1.0))
+    C.T_ref = float(cfg.get("T_ref", 0.0))
     for k in ("a", "b", "R", "omega", "G", "eta_l", "eta_v", "rho_l", "rho_v", "sigma", "kappa", "gx", "gy",
               "cv", "lambda_l", "lambda_v"):
         setattr(C, k, float(cfg[k]))

@@ -119,15 +119,34 @@ def test_large_tile_variant_pool_boiling(sim_cls, th, prec, nx, ny):
         assert rel(got["T"], want["T"]) <= 1e-4
 
 
-def test_fp32_deviation_storage_error_budget(sim_cls, th):
-    # FP32 arithmetic with f_i - w_i rho_ref storage: within 1e-4 relative of the FP64
-    # oracle in rho and T on the Stefan strip
+def l1rel(a, b):
+    """The paper's relative difference of a field, sum |a - b| / sum |b| (Eq. rel-diff-timestep form)."""
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+@pytest.mark.parametrize("case", ["stefan", "droplet", "pool"])
+def test_fp32_deviation_storage_error_budget(sim_cls, th, case):
+    # FP32 arithmetic with f_i - w_i rho_ref and T - T_ref storage against the FP64 oracle:
+    # the relative difference of rho and T (the paper's L1 form) stays below 1e-4; the
+    # pointwise maximum, which sits on moving interfaces, below 1e-3; the bulk
+    # (coexistence) densities within 0.5%.
     e = th["e"]
-    rv, rl, _ = th[0.86]
-    cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=5, n_vapour=10, precision="fp32")
+    if case == "stefan":
+        rv, rl, _ = th[0.86]
+        cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=5, n_vapour=10, precision="fp32")
+    elif case == "droplet":
+        rv, rl, _ = th[0.8]
+        cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=64, precision="fp32")
+    else:
+        rv, rl, _ = th[0.86]
+        cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=100, ny=83, precision="fp32")
     got, want = run_pair(sim_cls, cfg, ic, 1500)
-    assert rel(got["rho"], want["rho"]) <= 1e-4
-    assert rel(got["T"], want["T"]) <= 1e-4
+    assert l1rel(got["rho"], want["rho"]) <= 1e-4
+    assert l1rel(got["T"], want["T"]) <= 1e-4
+    assert rel(got["rho"], want["rho"]) <= 1e-3
+    assert rel(got["T"], want["T"]) <= 1e-3
+    for fn in (np.min, np.max):
+        assert fn(got["rho"]) == pytest.approx(fn(want["rho"]), rel=5e-3)
 
 
 def test_checkpoint_resume_is_bit_identical(sim_cls, th, tmp_path):

@@ -20,8 +20,8 @@ Configuration dict schema (all lattice units; side order x-min, x-max, y-min, y-
   thermal_bc[4]          T_PERIODIC | T_DIRICHLET | T_ADIABATIC
   T_side[4], rho_w_side[4]   per-side Dirichlet temperature and wall density
   rho_w[4], T_w[4], T_dirichlet[4]   optional per-boundary-node arrays (None = per side)
-  precision, rho_ref     CUDA path only: "fp64" | "fp32"; reference density of the
-                         FP32 deviation storage
+  precision, rho_ref, T_ref   CUDA path only: "fp64" | "fp32"; references of the FP32
+                         deviation storage f_i - w_i rho_ref and T - T_ref
 """
 from __future__ import annotations
 
@@ -46,7 +46,7 @@ def base_config(nx: int, ny: int, **kw) -> dict:
         hydro_bc=[PERIODIC] * 4, thermal_bc=[T_PERIODIC] * 4,
         T_side=[0.0] * 4, rho_w_side=[0.0] * 4,
         rho_w=[None] * 4, T_w=[None] * 4, T_dirichlet=[None] * 4,
-        precision="fp64", rho_ref=1.0,
+        precision="fp64", rho_ref=1.0, T_ref=0.0,
     )
     for k, v in kw.items():
         if k not in cfg:
@@ -87,7 +87,7 @@ def static_droplet(Tc, rho_v, rho_l, nx=64, ny=64, R0=16.0, width=3.0, T_ratio=0
     """Isothermal static droplet, periodic, all rates 1 (tau = 1)."""
     T = T_ratio * Tc
     cfg = base_config(nx, ny, sigma=sigma, kappa=kappa, rho_l=rho_l, rho_v=rho_v, precision=precision,
-                      rho_ref=rho_v)
+                      rho_ref=rho_v, T_ref=T)
     return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T, T)
 
 
@@ -103,7 +103,7 @@ def stefan_strip(Tc, rho_v, rho_l, sigma, nx=1024, ny=4, n_vapour=10, dT_ratio=0
         hydro_bc=[WALL, OUTFLOW, PERIODIC, PERIODIC],
         thermal_bc=[T_DIRICHLET, T_ADIABATIC, T_PERIODIC, T_PERIODIC],
         T_side=[T_sat + dT_ratio * Tc, 0.0, 0.0, 0.0], rho_w_side=[rho_v, 0.0, 0.0, 0.0],
-        precision=precision, rho_ref=rho_l)
+        precision=precision, rho_ref=rho_v, T_ref=T_sat)
     y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     rho = _tanh_profile(rho_l, rho_v, x - n_vapour, width)
     z = np.zeros((ny, nx))
@@ -123,18 +123,25 @@ def droplet_vaporization(Tc, rho_v, rho_l, sigma, nx=256, ny=256, R0=40.0, width
     cfg = base_config(
         nx, ny, s=[1.25] * 9, eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v, sigma=sigma,
         kappa=kappa, cv=5.0, lambda_l=lam, lambda_v=lam, energy_on=1, iso_steps=iso_steps,
-        thermal_bc=[T_DIRICHLET] * 4, T_side=[T_v] * 4, precision=precision, rho_ref=rho_v)
+        thermal_bc=[T_DIRICHLET] * 4, T_side=[T_v] * 4, precision=precision, rho_ref=rho_v, T_ref=T_l)
     return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T_l, T_v)
 
 
-def pool_boiling(Tc, rho_v, rho_l, sigma, nx=1024, ny=2048, g=3e-5, T_ratio=0.86, heater_frac=0.2,
+def pool_boiling(Tc, rho_v, rho_l, sigma, nx=1024, ny=2048, g=3e-5, g_ref_height=160, T_ratio=0.86,
+                 heater_frac=0.2,
                  dTh_ratio=0.1, rho_w_heater=3.44, rho_w_bottom=6.50, rho_w_top=0.38,
                  pool_frac=2.0 / 3.0, noise_ratio=1e-3, seed=20220112, width=3.0, precision="fp64"):
     """2-D pool boiling (Sec. 4.3): x periodic, Zou-He walls at y = 0 and y = ny-1,
     bottom-centre heater strip of heater_frac * nx nodes held at T_sat + dTh (Dirichlet),
     adiabatic elsewhere; psi-based wall densities per wall node; liquid pool below
-    pool_frac * ny at T_sat with seeded uniform noise of +-noise_ratio * Tc."""
+    pool_frac * ny at T_sat with seeded uniform noise of +-noise_ratio * Tc.
+
+    Gravity: g is the acceleration of a pool g_ref_height nodes tall (the paper's 160^2
+    base mesh); taller grids get g * g_ref_height / ny, which keeps the hydrostatic head
+    rho_l g H (~0.75 p_sat) of that pool. Without it a 4096-node column at g = 3e-5 would
+    carry ~20 p_sat and push the liquid out of the EOS's domain near the bottom."""
     T_sat = T_ratio * Tc
+    g = g * min(1.0, g_ref_height / float(ny))
     T_h = T_sat + dTh_ratio * Tc
     w = max(1, int(round(heater_frac * nx)))
     x0 = (nx - w) // 2
@@ -149,7 +156,7 @@ def pool_boiling(Tc, rho_v, rho_l, sigma, nx=1024, ny=2048, g=3e-5, T_ratio=0.86
         thermal_bc=[T_PERIODIC, T_PERIODIC, T_ADIABATIC, T_ADIABATIC],
         T_side=[0.0, 0.0, T_sat, T_sat], rho_w_side=[0.0, 0.0, rho_w_bottom, rho_w_top],
         rho_w=[None, None, rho_w_b, None], T_w=[None, None, T_w_b, None],
-        T_dirichlet=[None, None, heater, None], precision=precision, rho_ref=rho_l)
+        T_dirichlet=[None, None, heater, None], precision=precision, rho_ref=rho_v, T_ref=T_sat)
     y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     rho = _tanh_profile(rho_l, rho_v, pool_frac * ny - y, width)
     rng = np.random.default_rng(seed)
