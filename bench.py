@@ -166,6 +166,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=0, help="FP64 timed steps (default steps/8, >= 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
+    ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling runs; the bench workload is 2048)")
+    ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling runs; the bench workload is 4096)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -196,12 +200,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    nodes = NX * NY
+    nx, ny = args.nx, args.ny
+    nodes = nx * ny
     peaks, peak_kind = measured_peaks()
     out = {}
-    for prec in ("fp32", "fp64"):
+    precs = ("fp32", "fp64") if args.precision == "both" else (args.precision,)
+    for prec in precs:
         steps = args.steps if prec == "fp32" else (args.fp64_steps or max(8, args.steps // 8))
-        cfg, ic = workload(prec)
+        cfg, ic = workload(prec, nx=nx, ny=ny)
         sim = Simulation(cfg, *ic)
         sampler = ClockSampler(local) if prec == "fp32" else None
         barrier()
@@ -215,10 +221,10 @@ def main():
         n = sim.norms()
         out[prec] = {"dt": dt, "steps": steps, "launches": launches, "clocks": clocks, "flags": n["flags"],
                      "mass": n["mass"]}
-        if prec == "fp32":
+        if prec == "fp32" and not args.no_e2e:
             # end to end through the C ABI: pinned host inputs -> device, K steps, fields -> host
             host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory() for a in ic]
-            host_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+            host_out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(4)]
             import ctypes
             P = ctypes.POINTER(ctypes.c_double)
             sim.set_stream(None)
@@ -238,6 +244,11 @@ def main():
         torch.cuda.empty_cache()
 
     if rank != 0:
+        return
+    if args.precision != "both" or args.no_e2e:
+        # profiling / partial runs: timing summary only
+        print(json.dumps({p: {"mlups": world * nodes * v["steps"] / v["dt"] / 1e6, "ms_per_step": v["dt"] / v["steps"] * 1e3}
+                          for p, v in out.items() if p in ("fp32", "fp64")}))
         return
     f32, f64 = out["fp32"], out["fp64"]
     mlups32 = world * nodes * f32["steps"] / f32["dt"] / 1e6

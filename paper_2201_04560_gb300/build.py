@@ -10,8 +10,16 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libppl.so")
-SOURCES = [os.path.join(CSRC, "ppl.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "step_kernel.cuh"), os.path.join(ROOT, "include", "ppl.h")]
+# translation unit -> extra nvcc flags; the FP32 step uses approximate division and
+# square root (its error is budgeted against the FP64 oracle), the FP64 step is IEEE
+UNITS = {
+    "ppl.cu": [],
+    "step_fp64.cu": [],
+    "step_fp32.cu": ["--use_fast_math"],
+}
+SOURCES = [os.path.join(CSRC, u) for u in UNITS]
+DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "row_step.cuh", "step_variants.h")] + [
+    os.path.join(ROOT, "include", "ppl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,12 +37,20 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in DEPS):
             return LIB
+    nvcc = nvcc_path()
+    common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
+    objs, procs = [], []
+    for unit, extra in UNITS.items():
+        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        cmd = [nvcc, *common, *extra, "-c", os.path.join(CSRC, unit), "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    if any(p.wait() != 0 for p in procs):
+        raise RuntimeError("nvcc failed")
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc_path(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, *SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
     return LIB
 

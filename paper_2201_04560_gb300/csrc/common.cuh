@@ -1,0 +1,314 @@
+// Device-side building blocks of the coupled pseudopotential LBM + FD energy step
+// (arXiv 2201.04560, Sec. 2): parameter block, Peng-Robinson EOS and psi, boundary
+// classification, Zou-He closure, MRT collision with the Li source terms, and the FD
+// operator of the energy equation. Shared by the fused step kernel (row_step.cuh) and
+// the auxiliary kernels (initial state, export, norms).
+//
+// Populations are stored as deviations f~_i = f_i - w_i rho_ref and the temperature as
+// T - T_ref (rho_ref = T_ref = 0 for the FP64 path, so both precisions share one
+// arithmetic): the moments carry rho_ref only in m_0, m_1, m_2, which the collision
+// handles explicitly; the FD stencils act on the deviation directly and only the EOS
+// and the compression term use T_ref + (T - T_ref).
+#pragma once
+
+#include <cstdint>
+
+namespace ppl_dev {
+
+enum { PERIODIC = 0, WALL = 1, OUTFLOW = 2 };
+enum { T_PERIODIC = 0, T_DIRICHLET = 1, T_ADIABATIC = 2 };
+enum : unsigned { FLAG_PSI_NEG = 1u, FLAG_NAN = 2u, FLAG_RHO_NONPOS = 4u };
+
+template <typename real>
+struct Params {
+  int nx, ny;
+  long long plane;  // nx * ny
+  real a, b, R, Tc, k, G;
+  real sqrt_Tc_inv;  // 1/sqrt(Tc)
+  real s[9];
+  int var_eta;
+  real eta_l, eta_v, rho_l, rho_v, inv_drho;
+  real sigma12_e, sigma12_z;  // 12 sigma / (tau_e - 1/2), 12 sigma / (tau_zeta - 1/2)
+  real kappa_G2;              // kappa G / 2
+  real gx, gy, cv, lam_l, lam_v, dlam;  // dlam = (lam_l - lam_v)/(rho_l - rho_v)
+  int hbc[4], tbc[4];
+  real T_side[4], rho_w_side[4];
+  const real *rho_w[4];
+  const real *T_w[4];
+  const uint8_t *T_dir[4];
+  real rho_ref;
+  real T_ref;        // T is stored as T - T_ref (0 for the FP64 path)
+  real twoG_inv;     // 2 / G
+  real cv_inv;       // 1 / c_v
+  double inv_nodes;  // 1 / (nx ny)
+};
+
+struct StepIO {
+  const void *f_in;
+  const void *T_in;
+  void *f_out;
+  void *T_out;
+  const double *stats_in;  // [0] rho_bar of this step
+  double *stats_out;       // [0] rho_bar of the next step, [1] mass
+  double *partials;        // one FP64 partial per CTA
+  unsigned *counter;       // CTAs done (reset by the last one)
+  unsigned *status;        // PPL_FLAG_* bits
+};
+
+// lattice of Sec. 2
+__device__ __constant__ const int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ const int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+template <typename real>
+__device__ __forceinline__ real wgt(int i) {
+  return i == 0 ? real(4) / real(9) : (i < 5 ? real(1) / real(9) : real(1) / real(36));
+}
+
+// ---- Peng-Robinson EOS (Eq. peng-robinson) and the psi argument (Eq. psi) ----
+template <typename real>
+__device__ __forceinline__ real pr_alpha_root(const Params<real> &P, real T) {
+  return real(1) + P.k * (real(1) - sqrt(T) * P.sqrt_Tc_inv);
+}
+template <typename real>
+__device__ __forceinline__ real psi_arg(const Params<real> &P, real rho, real T) {
+  // p = rho R T / (1 - b rho) - a alpha rho^2 / (1 + 2 b rho - b^2 rho^2), over one denominator
+  const real ar = pr_alpha_root(P, T);
+  const real omb = real(1) - P.b * rho;
+  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
+  const real p = (rho * P.R * T * den - P.a * ar * ar * rho * rho * omb) / (omb * den);
+  return (p - rho * (real(1) / real(3))) * P.twoG_inv;
+}
+// rho-only parts of T (dp/dT)_rho = T A(rho) + k B(rho) (1 + k(1 - sqrt(T/Tc))) sqrt(T/Tc),
+// with A = rho R / (1 - b rho) and B = a rho^2 / (1 + 2 b rho - b^2 rho^2)
+template <typename real>
+__device__ __forceinline__ void dpdT_parts(const Params<real> &P, real rho, real *A, real *B) {
+  *A = rho * P.R / (real(1) - P.b * rho);
+  *B = P.a * rho * rho / (real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho);
+}
+template <typename real>
+__device__ __forceinline__ real T_dpdT(const Params<real> &P, real A, real B, real T) {
+  const real st = sqrt(T) * P.sqrt_Tc_inv;
+  return T * A + P.k * B * (real(1) + P.k * (real(1) - st)) * st;
+}
+
+// ---- boundary mapping of a (possibly out-of-domain) node coordinate ----
+// Periodic axes wrap. An outflow line and everything beyond it read the first interior
+// line (the zero-gradient copy). Beyond a wall the node is solid; its coordinates are
+// mirrored across the wall row so that rho, T (and u) ghosts of adiabatic walls read the
+// mirror image.
+struct NodeMap {
+  int x, y;
+  int solid;  // 1 if beyond a wall
+};
+
+template <typename real>
+__device__ __forceinline__ NodeMap map_node(const Params<real> &P, int gx, int gy) {
+  NodeMap m;
+  m.solid = 0;
+  const int nx = P.nx, ny = P.ny;
+  if (gx < 0 || gx >= nx) {
+    const int sd = gx < 0 ? 0 : 1;
+    const int k = P.hbc[sd];
+    if (k == PERIODIC) {
+      gx %= nx;
+      if (gx < 0) gx += nx;
+    } else if (k == OUTFLOW) {
+      gx = sd == 0 ? 1 : nx - 2;
+    } else {
+      m.solid = 1;
+      gx = sd == 0 ? -gx : 2 * (nx - 1) - gx;
+    }
+  } else if ((gx == nx - 1 && P.hbc[1] == OUTFLOW)) {
+    gx = nx - 2;
+  } else if (gx == 0 && P.hbc[0] == OUTFLOW) {
+    gx = 1;
+  }
+  if (gy < 0 || gy >= ny) {
+    const int sd = gy < 0 ? 2 : 3;
+    const int k = P.hbc[sd];
+    if (k == PERIODIC) {
+      gy %= ny;
+      if (gy < 0) gy += ny;
+    } else if (k == OUTFLOW) {
+      gy = sd == 2 ? 1 : ny - 2;
+    } else {
+      m.solid = 1;
+      gy = sd == 2 ? -gy : 2 * (ny - 1) - gy;
+    }
+  } else if (gy == ny - 1 && P.hbc[3] == OUTFLOW) {
+    gy = ny - 2;
+  } else if (gy == 0 && P.hbc[2] == OUTFLOW) {
+    gy = 1;
+  }
+  // ghosts far beyond a wall (ragged tiles) are never used; keep their address in range
+  m.x = min(max(gx, 0), nx - 1);
+  m.y = min(max(gy, 0), ny - 1);
+  return m;
+}
+
+template <typename real>
+__device__ __forceinline__ bool beyond_wall(const Params<real> &P, int gx, int gy) {
+  return (gx < 0 && P.hbc[0] == WALL) || (gx >= P.nx && P.hbc[1] == WALL) || (gy < 0 && P.hbc[2] == WALL) ||
+         (gy >= P.ny && P.hbc[3] == WALL);
+}
+
+// side of the wall a node lies on, or -1
+template <typename real>
+__device__ __forceinline__ int wall_side(const Params<real> &P, int gx, int gy) {
+  if (gx == 0 && P.hbc[0] == WALL) return 0;
+  if (gx == P.nx - 1 && P.hbc[1] == WALL) return 1;
+  if (gy == 0 && P.hbc[2] == WALL) return 2;
+  if (gy == P.ny - 1 && P.hbc[3] == WALL) return 3;
+  return -1;
+}
+
+template <typename real>
+__device__ __forceinline__ real wall_rho_w(const Params<real> &P, int side, int gx, int gy) {
+  const int pos = side < 2 ? gy : gx;
+  return P.rho_w[side] ? P.rho_w[side][pos] : P.rho_w_side[side];
+}
+
+// Dirichlet temperature node (y-sides decide at corners; thermally periodic sides skipped).
+// (gx, gy) must be in-domain coordinates (periodic images already wrapped).
+template <typename real>
+__device__ __forceinline__ int t_side_kind(const Params<real> &P, int sd, int pos, real *val) {
+  // -1: not a boundary for T (look further), 0: not Dirichlet, 1: Dirichlet
+  if (P.hbc[sd] == OUTFLOW) return 0;
+  if (P.hbc[sd] == PERIODIC && P.tbc[sd] == T_PERIODIC) return -1;
+  const bool dir = P.T_dir[sd] ? (P.T_dir[sd][pos] != 0) : (P.tbc[sd] == T_DIRICHLET);
+  if (!dir) return 0;
+  *val = P.T_w[sd] ? P.T_w[sd][pos] : P.T_side[sd];
+  return 1;
+}
+template <typename real>
+__device__ __forceinline__ bool t_fixed(const Params<real> &P, int gx, int gy, real *val) {
+  int r = -1;
+  if (gy == P.ny - 1) r = t_side_kind(P, 3, gx, val);
+  if (r < 0 && gy == 0) r = t_side_kind(P, 2, gx, val);
+  if (r < 0 && gx == P.nx - 1) r = t_side_kind(P, 1, gy, val);
+  if (r < 0 && gx == 0) r = t_side_kind(P, 0, gy, val);
+  return r == 1;
+}
+
+template <typename real>
+__device__ __forceinline__ bool is_outflow_line(const Params<real> &P, int gx, int gy) {
+  return (gx >= P.nx - 1 && P.hbc[1] == OUTFLOW) || (gx <= 0 && P.hbc[0] == OUTFLOW) ||
+         (gy >= P.ny - 1 && P.hbc[3] == OUTFLOW) || (gy <= 0 && P.hbc[2] == OUTFLOW);
+}
+
+// weight of a node in the domain sums: an outflow line is stored implicitly as a copy
+// of the first interior line, which therefore counts twice
+template <typename real>
+__device__ __forceinline__ double sum_weight(const Params<real> &P, int gx, int gy) {
+  double w = 1.0;
+  if (P.hbc[1] == OUTFLOW) { if (gx == P.nx - 1) w = 0.0; else if (gx == P.nx - 2) w *= 2.0; }
+  if (P.hbc[0] == OUTFLOW) { if (gx == 0) w = 0.0; else if (gx == 1) w *= 2.0; }
+  if (P.hbc[3] == OUTFLOW) { if (gy == P.ny - 1) w = 0.0; else if (gy == P.ny - 2) w *= 2.0; }
+  if (P.hbc[2] == OUTFLOW) { if (gy == 0) w = 0.0; else if (gy == 1) w *= 2.0; }
+  return w;
+}
+
+// ---- Zou-He no-slip wet node ----
+// Unknown populations (entering from the solid) from bounce-back of the normal
+// non-equilibrium part and the prescribed population momentum J = sum_i f_i c_i; no slip
+// with the half-force velocity (Eq. DensityAndVelocityRelationToF) is J = -F/2, F being
+// the wall node's force of the step that produced the populations. The w_i rho_ref parts
+// of opposite populations are equal, so the same closure holds for the deviations.
+template <typename real>
+__device__ __forceinline__ void zou_he(int side, real f[9], real Jx, real Jy) {
+  const real h = real(0.5), t23 = real(2) / real(3), s6 = real(1) / real(6);
+  if (side == 2) {
+    f[2] = f[4] + t23 * Jy;
+    f[5] = f[7] - h * (f[1] - f[3]) + s6 * Jy + h * Jx;
+    f[6] = f[8] + h * (f[1] - f[3]) + s6 * Jy - h * Jx;
+  } else if (side == 3) {
+    f[4] = f[2] - t23 * Jy;
+    f[7] = f[5] + h * (f[1] - f[3]) - s6 * Jy - h * Jx;
+    f[8] = f[6] - h * (f[1] - f[3]) - s6 * Jy + h * Jx;
+  } else if (side == 0) {
+    f[1] = f[3] + t23 * Jx;
+    f[5] = f[7] - h * (f[2] - f[4]) + s6 * Jx + h * Jy;
+    f[8] = f[6] + h * (f[2] - f[4]) + s6 * Jx - h * Jy;
+  } else {
+    f[3] = f[1] - t23 * Jx;
+    f[6] = f[8] - h * (f[2] - f[4]) - s6 * Jx + h * Jy;
+    f[7] = f[5] + h * (f[2] - f[4]) - s6 * Jx - h * Jy;
+  }
+}
+
+// ---- MRT collision in deviation form (Eqs. collisionMRT, li_source_terms, S, C) ----
+// fd: deviations f~ on entry, post-collision deviations on exit. rho = rho_ref + sum f~.
+template <typename real>
+__device__ __forceinline__ void collide(const Params<real> &P, real fd[9], real rho, real delta, real ux,
+                                        real uy, real Fx, real Fy, real Fm2_over_psi2, real Qxx, real Qyy,
+                                        real Qxy, real s_eta) {
+  // deviation moments m~ = M f~ (rows of M, Sec. 2)
+  const real ax = fd[1] + fd[2] + fd[3] + fd[4];
+  const real dg = fd[5] + fd[6] + fd[7] + fd[8];
+  const real m1 = -real(4) * fd[0] - ax + real(2) * dg;
+  const real m2 = real(4) * fd[0] - real(2) * ax + dg;
+  const real m3 = fd[1] - fd[3] + fd[5] - fd[6] - fd[7] + fd[8];
+  const real m4 = -real(2) * fd[1] + real(2) * fd[3] + fd[5] - fd[6] - fd[7] + fd[8];
+  const real m5 = fd[2] - fd[4] + fd[5] + fd[6] - fd[7] - fd[8];
+  const real m6 = -real(2) * fd[2] + real(2) * fd[4] + fd[5] + fd[6] - fd[7] - fd[8];
+  const real m7 = fd[1] - fd[2] + fd[3] - fd[4];
+  const real m8 = fd[5] - fd[6] + fd[7] - fd[8];
+  // non-equilibrium parts m - m^eq (m^eq = M f^eq of Eq. EquilibriumDistribution);
+  // the rho_ref w_i part contributes (rho_ref, -2 rho_ref, rho_ref, 0, ...) to m
+  const real u2 = ux * ux + uy * uy;
+  const real ru2 = rho * u2;
+  const real n1 = m1 + real(2) * delta - real(3) * ru2;
+  const real n2 = m2 - delta + real(3) * ru2;
+  const real n3 = m3 - rho * ux;
+  const real n4 = m4 + rho * ux;
+  const real n5 = m5 - rho * uy;
+  const real n6 = m6 + rho * uy;
+  const real n7 = m7 - rho * (ux * ux - uy * uy);
+  const real n8 = m8 - rho * ux * uy;
+  // Li forcing S (Eq. S, sigma term with |F^m|^2) and the kappa correction C (Eq. C)
+  const real uF = ux * Fx + uy * Fy;
+  const real S1 = real(6) * uF + P.sigma12_e * Fm2_over_psi2;
+  const real S2 = -real(6) * uF - P.sigma12_z * Fm2_over_psi2;
+  const real S7 = real(2) * (ux * Fx - uy * Fy);
+  const real S8 = ux * Fy + uy * Fx;
+  const real qs = Qxx + Qyy;
+  const real C1 = real(1.5) * P.s[1] * qs;
+  const real C2 = -real(1.5) * P.s[2] * qs;
+  const real C7 = -s_eta * (Qxx - Qyy);
+  const real C8 = -s_eta * Qxy;
+  // moment increments dm = -Lambda (m - m^eq) + (I - Lambda/2) S + C; dm_0 = 0 (S_0 = C_0 = 0),
+  // so f* = f + M^-1 dm leaves the mass untouched by construction (no rounding bias from
+  // the 1/9 scaling of the density row)
+  const real h = real(0.5);
+  const real d1 = -P.s[1] * n1 + (real(1) - h * P.s[1]) * S1 + C1;
+  const real d2 = -P.s[2] * n2 + (real(1) - h * P.s[2]) * S2 + C2;
+  const real d3 = -P.s[3] * n3 + (real(1) - h * P.s[3]) * Fx;
+  const real d4 = -P.s[4] * n4 - (real(1) - h * P.s[4]) * Fx;
+  const real d5 = -P.s[5] * n5 + (real(1) - h * P.s[5]) * Fy;
+  const real d6 = -P.s[6] * n6 - (real(1) - h * P.s[6]) * Fy;
+  const real d7 = -s_eta * n7 + (real(1) - h * s_eta) * S7 + C7;
+  const real d8 = -s_eta * n8 + (real(1) - h * s_eta) * S8 + C8;
+  // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  const real a1 = d1 * (real(1) / real(36)), a2 = d2 * (real(1) / real(36));
+  const real a3 = d3 * (real(1) / real(6)), a4 = d4 * (real(1) / real(12)), a5 = d5 * (real(1) / real(6));
+  const real a6 = d6 * (real(1) / real(12)), a7 = d7 * real(0.25), a8 = d8 * real(0.25);
+  const real ca = -a1 - real(2) * a2;
+  const real cd = real(2) * a1 + a2;
+  fd[0] += -real(4) * a1 + real(4) * a2;
+  fd[1] += ca + a3 - real(2) * a4 + a7;
+  fd[2] += ca + a5 - real(2) * a6 - a7;
+  fd[3] += ca - a3 + real(2) * a4 + a7;
+  fd[4] += ca - a5 + real(2) * a6 - a7;
+  fd[5] += cd + a3 + a4 + a5 + a6 + a8;
+  fd[6] += cd - a3 - a4 + a5 + a6 - a8;
+  fd[7] += cd - a3 - a4 - a5 - a6 + a8;
+  fd[8] += cd + a3 + a4 - a5 - a6 - a8;
+}
+
+template <typename real>
+__device__ __forceinline__ real ld_real(const void *p, long long k) {
+  return __ldg(reinterpret_cast<const real *>(p) + k);
+}
+
+
+}  // namespace ppl_dev

@@ -1,6 +1,7 @@
 // Host side of libppl: the C ABI declared in include/ppl.h, device buffers, CUDA-graph
 // step chunks, and the auxiliary kernels (initial state, field export, FP64 norms).
-// The hot path is the fused step kernel of step_kernel.cuh.
+// The hot path is the fused step kernel of row_step.cuh (instantiated in step_fp32.cu and
+// step_fp64.cu).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -11,7 +12,8 @@
 #include <vector>
 
 #include "../../include/ppl.h"
-#include "step_kernel.cuh"
+#include "common.cuh"
+#include "step_variants.h"
 
 using namespace ppl_dev;
 
@@ -193,28 +195,6 @@ __global__ void export_populations(const Params<real> P, const real *f, double *
   }
 }
 
-// ---------------------------------------------------------------------------------
-// kernel variants
-// ---------------------------------------------------------------------------------
-
-struct Variant {
-  int tx, ty, nt;
-  size_t smem;
-  const void *fn[2];  // [energy]
-};
-
-template <typename real, int TX, int TY, int NT>
-Variant make_variant() {
-  Variant v;
-  v.tx = TX;
-  v.ty = TY;
-  v.nt = NT;
-  v.smem = step_smem_bytes<real, TX, TY>();
-  v.fn[0] = (const void *)fused_step<real, false, TX, TY, NT>;
-  v.fn[1] = (const void *)fused_step<real, true, TX, TY, NT>;
-  return v;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -244,8 +224,9 @@ struct ppl_sim {
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [energy], captured from parity 0
-  Variant var;
+  StepVariant var;
   dim3 grid;
+  int rows_per_cta = 0;
   int stats_blocks = 0;
   Params<double> pd;
   Params<float> pf;
@@ -354,6 +335,8 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
   P.Tc = (real)Tc;
   P.k = (real)(0.37464 + 1.54226 * c.omega - 0.2699 * c.omega * c.omega);
   P.G = (real)c.G;
+  P.twoG_inv = (real)(2.0 / c.G);
+  P.cv_inv = (real)(1.0 / c.cv);
   P.sqrt_Tc_inv = (real)(1.0 / std::sqrt(Tc));
   for (int i = 0; i < 9; ++i) P.s[i] = (real)c.s[i];
   P.var_eta = (c.eta_l > 0 && c.eta_v > 0) ? 1 : 0;
@@ -406,7 +389,8 @@ int launch_step_t(ppl_sim *h, bool energy) {
   io.partials = h->partials;
   io.counter = h->counter;
   io.status = h->status;
-  void *args[] = {(void *)&P, (void *)&io};
+  int H = h->rows_per_cta;
+  void *args[] = {(void *)&P, (void *)&io, (void *)&H};
   CK(cudaLaunchKernel(h->var.fn[energy ? 1 : 0], h->grid, dim3(h->var.nt), args, h->var.smem, h->stream));
   h->cur = 1 - h->cur;
   h->step += 1;
@@ -646,22 +630,26 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PPL_E_CUDA);
   h->stream = h->own_stream;
 
-  // kernel variant: the large tile unless the grid would give fewer than ~2 CTAs per SM
-  Variant big, small;
-  if (h->prec == PPL_FP64) {
-    big = make_variant<double, 32, 16, 256>();
-    small = make_variant<double, 16, 8, 128>();
-  } else {
-    big = make_variant<float, 64, 16, 256>();
-    small = make_variant<float, 32, 8, 128>();
-  }
-  const long long big_ctas = (long long)((h->nx + big.tx - 1) / big.tx) * ((h->ny + big.ty - 1) / big.ty);
-  h->var = big_ctas >= 304 ? big : small;
-  h->grid = dim3((h->nx + h->var.tx - 1) / h->var.tx, (h->ny + h->var.ty - 1) / h->var.ty);
+  // launch shape: strips of (nt - 6) columns, one wave of CTAs over the rows
+  h->var = h->prec == PPL_FP64 ? step_variant_fp64() : step_variant_fp32();
   for (int e = 0; e < 2; ++e)
     if (cudaFuncSetAttribute(h->var.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->var.smem) !=
         cudaSuccess)
       return fail(PPL_E_CUDA);
+  {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->var.fn[1], h->var.nt, h->var.smem);
+    const int slots = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    const int strips = (h->nx + (h->var.nt - 6) - 1) / (h->var.nt - 6);
+    int yblocks = slots / strips;
+    if (yblocks < 1) yblocks = 1;
+    int H = (h->ny + yblocks - 1) / yblocks;
+    if (H < 8) H = 8;
+    h->rows_per_cta = H;
+    h->grid = dim3(strips, (h->ny + H - 1) / H);
+  }
   h->stats_blocks = 608;
   const size_t nctas = (size_t)h->grid.x * h->grid.y;
   const size_t npart = nctas > (size_t)h->stats_blocks * 7 ? nctas : (size_t)h->stats_blocks * 7;

@@ -1,0 +1,445 @@
+// Fused time step of the coupled pseudopotential LBM + FD energy equation
+// (arXiv 2201.04560, Sec. 2) for sm_103a: the row-marching pipeline.
+//
+// A CTA owns a strip of NT columns (NT - 6 interior columns plus a 3-column halo on each
+// side) and H rows. One thread per column marches up the rows; rows are staged
+// asynchronously into shared memory PF rows ahead (cp.async), and every iteration runs
+// four stages at fixed row lags:
+//   S1 (row q):   rho, j = sum f c, psi(rho, T)                       Eqs. (psi), (peng-robinson)
+//   S2 (row q-1): F^m with the psi-based wall form, F^b, u             Eqs. (shanchen), (shanchen-walls),
+//                                                                      (psi-based-formula), (gravitational_force),
+//                                                                      (DensityAndVelocityRelationToF)
+//   S3 (row q-2): Q and the MRT collision with the Li source terms;    Eqs. (Q), (Q-psi-based), (collisionMRT),
+//                 first Heun stage of the energy equation              (li_source_terms), (S), (C), (energy-equation)
+//   S4 (row q-3): pull streaming f(x) = f*(x - c_i), Zou-He, second   Eq. (lbm), Sec. 2.2
+//                 Heun stage, store, FP64 mass partial
+// Per-row quantities live in small shared-memory ring buffers (rows q-3..q), so every
+// node is computed once per CTA; only the x-halo columns and 3 rows at each end of the
+// strip are recomputed. DRAM traffic is one read and one write of (f, T) per node.
+#pragma once
+
+#include "common.cuh"
+
+namespace ppl_dev {
+
+// classification of a line index g (a column or a row) against its axis boundaries
+struct LineMap {
+  int src;      // in-domain line the node's state is read from (wrap, outflow copy, wall mirror)
+  int solid;    // beyond a wall
+  int wall;     // side index if this line is a wall line, else -1
+  int outflow;  // an outflow line or beyond: an implicit copy of the first interior line
+};
+
+__device__ __forceinline__ LineMap map_line(int g, int n, int bc_lo, int bc_hi, int side_lo) {
+  LineMap m;
+  m.solid = 0;
+  m.wall = -1;
+  m.outflow = 0;
+  if (g < 0 || g >= n) {
+    const int k = g < 0 ? bc_lo : bc_hi;
+    if (k == PERIODIC) {
+      g %= n;
+      if (g < 0) g += n;
+    } else if (k == OUTFLOW) {
+      m.outflow = 1;
+      g = g < 0 ? 1 : n - 2;
+    } else {
+      m.solid = 1;
+      g = g < 0 ? -g : 2 * (n - 1) - g;
+      g = min(max(g, 0), n - 1);  // far ghosts of ragged strips are never used
+    }
+  } else {
+    if (g == 0 && bc_lo == WALL) m.wall = side_lo;
+    else if (g == n - 1 && bc_hi == WALL) m.wall = side_lo + 1;
+    if (g == n - 1 && bc_hi == OUTFLOW) {
+      m.outflow = 1;
+      g = n - 2;
+    } else if (g == 0 && bc_lo == OUTFLOW) {
+      m.outflow = 1;
+      g = 1;
+    }
+  }
+  m.src = g;
+  return m;
+}
+
+// mass-sum weight of a line: the first interior line also stands for its outflow copy
+__device__ __forceinline__ double line_weight(int g, int n, int bc_lo, int bc_hi) {
+  double w = 1.0;
+  if (bc_hi == OUTFLOW && g == n - 2) w += 1.0;
+  if (bc_lo == OUTFLOW && g == 1) w += 1.0;
+  return w;
+}
+
+template <typename real>
+__device__ __forceinline__ void cp_async_real(real *smem_dst, const real *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(real) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename real>
+struct S4Carry {  // per-node values handed from S3 (row r) to S4 (row r, next iteration)
+  real k1, lam, gdx, gdy, div, inv_rcv, ux, uy, A, B, Fx, Fy;
+};
+
+template <int NT, int PF, typename real>
+constexpr size_t row_step_smem_bytes() {
+  return (size_t)((PF + 3) * 10 + 9 * 4 + 27 + 3) * NT * sizeof(real);
+}
+
+template <typename real, bool ENERGY, int NT, int PF>
+__global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepIO io, const int H) {
+  constexpr int D = PF + 3;  // staging depth in rows
+  constexpr int W = NT - 6;  // interior columns per strip
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *stg = reinterpret_cast<real *>(smem_raw);  // [D][10][NT]: f_0..f_8, T of staged rows
+  real *rpsi = stg + D * 10 * NT;                   // rings [4][NT] indexed by row mod 4
+  real *rrho = rpsi + 4 * NT;
+  real *rT = rrho + 4 * NT;
+  real *rjx = rT + 4 * NT;
+  real *rjy = rjx + 4 * NT;
+  real *rux = rjy + 4 * NT;
+  real *ruy = rux + 4 * NT;
+  real *rfx = ruy + 4 * NT;  // F^m
+  real *rfy = rfx + 4 * NT;
+  real *rfs = rfy + 4 * NT;  // [3][9][NT] post-collision populations, row mod 3
+  real *rTs = rfs + 27 * NT; // [3][NT] first Heun stage T*, row mod 3
+
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * W;
+  const int ya = blockIdx.y * H;
+  const int yb = min(ya + H, P.ny);
+  const int gx = x0 - 3 + t;
+  const LineMap cm = map_line(gx, P.nx, P.hbc[0], P.hbc[1], 0);
+  const long long plane = P.plane;
+  const real rho_bar = real(io.stats_in[0]);
+  const bool xwall_strip = (P.hbc[0] == WALL && x0 - 3 < 0) || (P.hbc[1] == WALL && x0 + W + 3 > P.nx - 1);
+  const bool xout_strip = (P.hbc[0] == OUTFLOW && x0 - 3 <= 0) || (P.hbc[1] == OUTFLOW && x0 + W + 3 >= P.nx - 1);
+  const bool t_s2 = t >= 1 && t < NT - 1;
+  const bool t_s3 = t >= 2 && t < NT - 2;
+  const bool t_s4 = t >= 3 && t < NT - 3 && gx < P.nx && !cm.solid && !cm.outflow;
+  const double wcol = line_weight(gx, P.nx, P.hbc[0], P.hbc[1]);
+  const real *fin = reinterpret_cast<const real *>(io.f_in);
+  const real *Tin = reinterpret_cast<const real *>(io.T_in);
+  real *fout = reinterpret_cast<real *>(io.f_out);
+  real *Tout = reinterpret_cast<real *>(io.T_out);
+  const int n_it = yb - ya + 6;  // rows ya-3 .. yb+2 pass through S1
+  unsigned flags = 0;
+  double acc = 0.0;
+
+  auto stage_row = [&](int q, int slot) {
+    const LineMap rm = map_line(q, P.ny, P.hbc[2], P.hbc[3], 2);
+    const long long k = (long long)rm.src * P.nx + cm.src;
+    real *dst = stg + slot * 10 * NT + t;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cp_async_real(dst + i * NT, fin + i * plane + k);
+    cp_async_real(dst + 9 * NT, Tin + k);
+  };
+
+#pragma unroll
+  for (int j = 0; j < PF; ++j) {
+    if (j < n_it) stage_row(ya - 3 + j, j);
+    cp_async_commit();
+  }
+
+  S4Carry<real> cur{}, nxt{};
+  for (int iq = 0; iq < n_it; ++iq) {
+    const int q = ya - 3 + iq;
+    if (iq + PF < n_it) stage_row(q + PF, (iq + PF) % D);
+    cp_async_commit();
+    cp_async_wait<PF>();  // this thread's copies of row q have landed
+    const int s4_0 = iq & 3, s4_1 = (iq + 3) & 3, s4_2 = (iq + 2) & 3, s4_3 = (iq + 1) & 3;  // rows q, q-1, q-2, q-3
+    const int f_r2 = (iq + 1) % 3, f_r3 = iq % 3, f_r4 = (iq + 2) % 3;  // f*/T* ring: rows q-2, q-3, q-4
+
+    // ---- S1: row q ----
+    {
+      const LineMap rm = map_line(q, P.ny, P.hbc[2], P.hbc[3], 2);
+      const real *st = stg + (iq % D) * 10 * NT + t;
+      real f[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = st[i * NT];
+      const real Tt = st[9 * NT];
+      const real delta = ((f[0] + (f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
+      const real rho = P.rho_ref + delta;
+      real psi = real(0);
+      if (!cm.solid && !rm.solid) {
+        const real arg = psi_arg(P, rho, P.T_ref + Tt);
+        if (!(arg >= real(0))) flags |= FLAG_PSI_NEG;
+        psi = sqrt(fmax(arg, real(0)));
+      }
+      const int i0 = s4_0 * NT + t;
+      rpsi[i0] = psi;
+      rrho[i0] = rho;
+      rT[i0] = Tt;
+      rjx[i0] = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+      rjy[i0] = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    }
+    __syncthreads();
+
+    // ---- S2: row q-1 ----
+    if (iq >= 2) {
+      const int r = q - 1;
+      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      const int i0 = s4_1 * NT + t, iu = s4_0 * NT + t, id = s4_2 * NT + t;
+      if (t_s2) {
+        if (!cm.solid && !rm.solid) {
+          const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
+          const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
+          const real third = real(1) / real(3), twelfth = real(1) / real(12);
+          real sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
+          real sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
+          const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
+          if (ws >= 0) {
+            // solid links (psi = 0 in the ring) carry psi_w = psi(rho_w, T); their weights
+            // sum to 1/2 along the outward normal
+            const real argw = psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]);
+            if (!(argw >= real(0))) flags |= FLAG_PSI_NEG;
+            const real hw = real(0.5) * sqrt(fmax(argw, real(0)));
+            if (ws == 0) sx -= hw;
+            else if (ws == 1) sx += hw;
+            else if (ws == 2) sy -= hw;
+            else sy += hw;
+          }
+          const real psi_c = rpsi[i0];
+          const real rho = rrho[i0];
+          const real fmx = -P.G * psi_c * sx, fmy = -P.G * psi_c * sy;
+          const real Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
+          const real inv_rho = real(1) / rho;
+          const real ux = (rjx[i0] + real(0.5) * Fx) * inv_rho;
+          const real uy = (rjy[i0] + real(0.5) * Fy) * inv_rho;
+          rux[i0] = ux;
+          ruy[i0] = uy;
+          rfx[i0] = fmx;
+          rfy[i0] = fmy;
+          if (ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
+            rux[s4_3 * NT + t] = ux;
+            ruy[s4_3 * NT + t] = -uy;
+          }
+        } else if (ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny
+          rux[i0] = rux[s4_3 * NT + t];
+          ruy[i0] = -ruy[s4_3 * NT + t];
+        }
+      }
+      __syncthreads();
+      if (ENERGY && xwall_strip) {
+        if (t_s2) {
+          int src = -1;
+          if (P.hbc[0] == WALL && gx == -1) src = t + 2;
+          else if (P.hbc[1] == WALL && gx == P.nx) src = t - 2;
+          if (src >= 1 && src < NT - 1) {
+            rux[i0] = -rux[s4_1 * NT + src];
+            ruy[i0] = ruy[s4_1 * NT + src];
+          }
+        }
+        __syncthreads();
+      }
+    }
+
+    // ---- S3: row q-2 ----
+    if (iq >= 4) {
+      const int r = q - 2;
+      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      const int i0 = s4_2 * NT + t, iu = s4_1 * NT + t, id = s4_3 * NT + t;
+      if (t_s3) {
+        if (!cm.solid && !rm.solid) {
+          const real *st = stg + ((iq + D - 2) % D) * 10 * NT + t;
+          real fd[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) fd[i] = st[i * NT];
+          // the mass moment is the exact sum of the stored deviations (rho_ref + delta is
+          // rounded to the precision of rho)
+          const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
+          const real rho = rrho[i0];
+          const real psi_c = rpsi[i0];
+          // Q (Eq. Q), solid links through psi_w (Eq. Q-psi-based)
+          const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
+          const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
+          const real third = real(1) / real(3), twelfth = real(1) / real(12);
+          const real dsum = twelfth * (p5 + p6 + p7 + p8 - real(4) * psi_c);
+          real qxx = third * (p1 + p3 - real(2) * psi_c) + dsum;
+          real qyy = third * (p2 + p4 - real(2) * psi_c) + dsum;
+          real qxy = twelfth * (p5 - p6 + p7 - p8);
+          const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
+          if (ws >= 0) {
+            const real psi_w = sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]), real(0)));
+            if (ws < 2) {
+              qxx += real(0.5) * psi_w;
+              qyy += (real(1) / real(6)) * psi_w;
+            } else {
+              qxx += (real(1) / real(6)) * psi_w;
+              qyy += real(0.5) * psi_w;
+            }
+          }
+          const real qf = P.kappa_G2 * psi_c;
+          qxx *= qf;
+          qyy *= qf;
+          qxy *= qf;
+          const real fmx = rfx[i0], fmy = rfy[i0];
+          const real ux = rux[i0], uy = ruy[i0];
+          const real Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
+          const real inv_psi = real(1) / psi_c;
+          const real fm2 = (fmx * fmx + fmy * fmy) * (inv_psi * inv_psi);
+          real s_eta = P.s[7];
+          if (P.var_eta) s_eta = real(1) / (real(3) * (P.eta_v + (P.eta_l - P.eta_v) * (rho - P.rho_v) * P.inv_drho) + real(0.5));
+          collide(P, fd, rho, delta, ux, uy, Fx, Fy, fm2, qxx, qyy, qxy, s_eta);
+          real *fs = rfs + f_r2 * 9 * NT + t;
+#pragma unroll
+          for (int i = 0; i < 9; ++i) fs[i * NT] = fd[i];
+          nxt.Fx = Fx;
+          nxt.Fy = Fy;
+          if (ENERGY) {
+            real Tw, Ts;
+            const real T0 = rT[i0];
+            const real inv_rho = real(1) / rho;
+            nxt.ux = ux;
+            nxt.uy = uy;
+            dpdT_parts(P, rho, &nxt.A, &nxt.B);
+            nxt.inv_rcv = inv_rho * P.cv_inv;
+            nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
+            // frozen coefficients of Eq. (energy-equation): grad lambda = dlam grad rho, div u
+            const real r1 = rrho[i0 + 1], r3 = rrho[i0 - 1], r2 = rrho[iu], r4 = rrho[id];
+            const real r5 = rrho[iu + 1], r6 = rrho[iu - 1], r7 = rrho[id - 1], r8 = rrho[id + 1];
+            nxt.gdx = P.dlam * (third * (r1 - r3) + twelfth * (r5 - r6 - r7 + r8));
+            nxt.gdy = P.dlam * (third * (r2 - r4) + twelfth * (r5 + r6 - r7 - r8));
+            nxt.div = third * (rux[i0 + 1] - rux[i0 - 1]) +
+                      twelfth * (rux[iu + 1] - rux[iu - 1] - rux[id - 1] + rux[id + 1]) +
+                      third * (ruy[iu] - ruy[id]) + twelfth * (ruy[iu + 1] + ruy[iu - 1] - ruy[id - 1] - ruy[id + 1]);
+            if (t_fixed(P, cm.src, rm.src, &Tw)) {
+              Ts = Tw - P.T_ref;
+              nxt.k1 = real(0);
+            } else if (rm.outflow) {
+              Ts = rTs[f_r3 * NT + t];  // outflow row: copy of the first interior row
+              nxt.k1 = real(0);
+            } else {
+              const real t1 = rT[i0 + 1], t3 = rT[i0 - 1], t2 = rT[iu], t4 = rT[id];
+              const real t5 = rT[iu + 1], t6 = rT[iu - 1], t7 = rT[id - 1], t8 = rT[id + 1];
+              const real gtx = third * (t1 - t3) + twelfth * (t5 - t6 - t7 + t8);
+              const real gty = third * (t2 - t4) + twelfth * (t5 + t6 - t7 - t8);
+              const real lap = (real(2) / real(3)) * (t1 + t2 + t3 + t4 - real(4) * T0) +
+                               (real(1) / real(6)) * (t5 + t6 + t7 + t8 - real(4) * T0);
+              const real k1 = -(ux * gtx + uy * gty) + (nxt.lam * lap + nxt.gdx * gtx + nxt.gdy * gty) * nxt.inv_rcv -
+                              T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0) * nxt.div * nxt.inv_rcv;
+              nxt.k1 = k1;
+              Ts = T0 + k1;
+            }
+            rTs[f_r2 * NT + t] = Ts;
+            if (r == 1 && P.hbc[2] == WALL) rTs[f_r4 * NT + t] = Ts;  // mirror ghost of row -1
+          }
+        } else if (ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {
+          rTs[f_r2 * NT + t] = rTs[f_r4 * NT + t];  // mirror ghost of row ny (copy of row ny-2)
+        }
+      }
+      __syncthreads();
+      if (ENERGY && (xwall_strip || xout_strip)) {
+        if (t_s3) {
+          int src = -1;
+          if (P.hbc[0] == WALL && gx == -1) src = t + 2;
+          else if (P.hbc[1] == WALL && gx == P.nx) src = t - 2;
+          else if (P.hbc[1] == OUTFLOW && gx >= P.nx - 1) src = t - (gx - (P.nx - 2));
+          else if (P.hbc[0] == OUTFLOW && gx <= 0) src = t + (1 - gx);
+          if (src >= 2 && src < NT - 2) rTs[f_r2 * NT + t] = rTs[f_r2 * NT + src];
+        }
+        __syncthreads();
+      }
+    }
+
+    // ---- S4: row q-3 ----
+    if (iq >= 6 && t_s4) {
+      const int r = q - 3;
+      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      if (!rm.outflow) {
+        // pull: f_i(x) = f*_i(x - c_i); ring rows r-1, r, r+1 are slots f_r4, f_r3, f_r2
+        const real *lo = rfs + f_r4 * 9 * NT + t, *mid = rfs + f_r3 * 9 * NT + t, *hi = rfs + f_r2 * 9 * NT + t;
+        real fd[9];
+        fd[0] = mid[0];
+        fd[1] = mid[1 * NT - 1];
+        fd[2] = lo[2 * NT];
+        fd[3] = mid[3 * NT + 1];
+        fd[4] = hi[4 * NT];
+        fd[5] = lo[5 * NT - 1];
+        fd[6] = lo[6 * NT + 1];
+        fd[7] = hi[7 * NT + 1];
+        fd[8] = hi[8 * NT - 1];
+        const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
+        if (ws >= 0) zou_he(ws, fd, -real(0.5) * cur.Fx, -real(0.5) * cur.Fy);
+        const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
+        const real rho_new = P.rho_ref + delta;
+        const int i3 = s4_3 * NT + t;
+        real T_new = rT[i3];
+        if (ENERGY) {
+          real Tw;
+          if (!t_fixed(P, cm.src, rm.src, &Tw)) {
+            const real *m0 = rTs + f_r3 * NT + t, *u0 = rTs + f_r2 * NT + t, *d0 = rTs + f_r4 * NT + t;
+            const real c = m0[0];
+            const real t1 = m0[1], t3 = m0[-1], t2 = u0[0], t4 = d0[0];
+            const real t5 = u0[1], t6 = u0[-1], t7 = d0[-1], t8 = d0[1];
+            const real third = real(1) / real(3), twelfth = real(1) / real(12);
+            const real gtx = third * (t1 - t3) + twelfth * (t5 - t6 - t7 + t8);
+            const real gty = third * (t2 - t4) + twelfth * (t5 + t6 - t7 - t8);
+            const real lap = (real(2) / real(3)) * (t1 + t2 + t3 + t4 - real(4) * c) +
+                             (real(1) / real(6)) * (t5 + t6 + t7 + t8 - real(4) * c);
+            const real k2 = -(cur.ux * gtx + cur.uy * gty) + (cur.lam * lap + cur.gdx * gtx + cur.gdy * gty) * cur.inv_rcv -
+                            T_dpdT(P, cur.A, cur.B, P.T_ref + c) * cur.div * cur.inv_rcv;
+            T_new = T_new + real(0.5) * (cur.k1 + k2);
+          }
+        }
+        const long long k = (long long)r * P.nx + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fout[i * plane + k] = fd[i];
+        Tout[k] = T_new;
+        if (!(rho_new == rho_new) || !(T_new == T_new) || isinf((double)rho_new) || isinf((double)T_new)) flags |= FLAG_NAN;
+        if (!(rho_new > real(0))) flags |= FLAG_RHO_NONPOS;
+        acc += wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]) * (double)rho_new;
+      }
+    }
+    cur = nxt;
+  }
+  cp_async_wait<0>();
+  if (flags) atomicOr(io.status, flags);
+
+  // ---- deterministic FP64 reduction of sum rho^{n+1} ----
+  __shared__ double red[NT / 32];
+  __shared__ bool am_last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((t & 31) == 0) red[t >> 5] = acc;
+  __syncthreads();
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    io.partials[bid] = s;
+    __threadfence();
+    const unsigned done = atomicAdd(io.counter, 1u);
+    am_last = (done == nblk - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned b = t; b < nblk; b += NT) s += __ldcg(io.partials + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((t & 31) == 0) red[t >> 5] = s;
+    __syncthreads();
+    if (t == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < NT / 32; ++w) tot += red[w];
+      io.stats_out[0] = tot * P.inv_nodes;
+      io.stats_out[1] = tot;
+      *io.counter = 0u;
+    }
+  }
+}
+
+}  // namespace ppl_dev

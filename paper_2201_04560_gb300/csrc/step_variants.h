@@ -1,0 +1,22 @@
+// Launch shapes of the fused row step and the host-side handles of its instantiations.
+#pragma once
+
+#include <cstddef>
+
+namespace ppl_dev {
+
+constexpr int kNT32 = 128;  // threads (columns incl. the 3 + 3 halo) per CTA, FP32
+constexpr int kPF32 = 2;    // rows staged ahead, FP32
+constexpr int kNT64 = 128;
+constexpr int kPF64 = 2;
+
+struct StepVariant {
+  int nt;        // threads per CTA = strip width incl. halo
+  size_t smem;   // dynamic shared memory per CTA
+  const void *fn[2];  // [energy on]
+};
+
+StepVariant step_variant_fp32();
+StepVariant step_variant_fp64();
+
+}  // namespace ppl_dev

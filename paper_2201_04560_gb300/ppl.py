@@ -60,15 +60,21 @@ def library_path() -> str:
 
 
 def load_library(build_if_missing: bool = True):
-    """Load libppl.so (building it in-tree with nvcc when it is missing or stale)."""
+    """Load libppl.so (building it in-tree with nvcc when it is missing or stale).
+
+    The environment variable PPL_LIBRARY names another build of the library to load
+    instead (no build step then)."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing:
-        _build.build_library()
-    if not os.path.exists(_build.LIB):
+    path = os.environ.get("PPL_LIBRARY")
+    if not path:
+        if build_if_missing:
+            _build.build_library()
+        path = _build.LIB
+    if not os.path.exists(path):
         raise RuntimeError("libppl.so is not built (run __graft_entry__.build())")
-    L = ctypes.CDLL(_build.LIB)
+    L = ctypes.CDLL(path)
     H = ctypes.c_void_p
     L.ppl_init.argtypes = [ctypes.POINTER(PplConfig), _PD, _PD, _PD, _PD, ctypes.POINTER(H)]
     L.ppl_reset.argtypes = [H, _PD, _PD, _PD, _PD]
