@@ -79,11 +79,14 @@ __device__ __forceinline__ real psi_arg(const Params<real> &P, real rho, real T)
   return (p - rho * (real(1) / real(3))) * P.twoG_inv;
 }
 // rho-only parts of T (dp/dT)_rho = T A(rho) + k B(rho) (1 + k(1 - sqrt(T/Tc))) sqrt(T/Tc),
-// with A = rho R / (1 - b rho) and B = a rho^2 / (1 + 2 b rho - b^2 rho^2)
+// with A = rho R / (1 - b rho) and B = a rho^2 / (1 + 2 b rho - b^2 rho^2) (one division)
 template <typename real>
 __device__ __forceinline__ void dpdT_parts(const Params<real> &P, real rho, real *A, real *B) {
-  *A = rho * P.R / (real(1) - P.b * rho);
-  *B = P.a * rho * rho / (real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho);
+  const real omb = real(1) - P.b * rho;
+  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
+  const real inv = real(1) / (omb * den);
+  *A = rho * P.R * den * inv;
+  *B = P.a * rho * rho * omb * inv;
 }
 template <typename real>
 __device__ __forceinline__ real T_dpdT(const Params<real> &P, real A, real B, real T) {

@@ -86,13 +86,17 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 template <typename real>
-struct S4Carry {  // per-node values handed from S3 (row r) to S4 (row r, next iteration)
+struct S3Carry {  // S2 (row r) -> S3 (row r, next iteration)
+  real fmx, fmy, fm2, inv_rho;  // F^m, |F^m|^2 / psi^2 = G^2 |s|^2, 1/rho
+};
+template <typename real>
+struct S4Carry {  // S3 (row r) -> S4 (row r, next iteration)
   real k1, lam, gdx, gdy, div, inv_rcv, ux, uy, A, B, Fx, Fy;
 };
 
 template <int NT, int PF, typename real>
 constexpr size_t row_step_smem_bytes() {
-  return (size_t)((PF + 3) * 10 + 9 * 4 + 27 + 3) * NT * sizeof(real);
+  return (size_t)((PF + 3) * 10 + 5 * 4 + 27 + 3) * NT * sizeof(real);
 }
 
 template <typename real, bool ENERGY, int NT, int PF>
@@ -104,14 +108,12 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
   real *rpsi = stg + D * 10 * NT;                   // rings [4][NT] indexed by row mod 4
   real *rrho = rpsi + 4 * NT;
   real *rT = rrho + 4 * NT;
-  real *rjx = rT + 4 * NT;
-  real *rjy = rjx + 4 * NT;
-  real *rux = rjy + 4 * NT;
+  real *rux = rT + 4 * NT;
   real *ruy = rux + 4 * NT;
-  real *rfx = ruy + 4 * NT;  // F^m
-  real *rfy = rfx + 4 * NT;
-  real *rfs = rfy + 4 * NT;  // [3][9][NT] post-collision populations, row mod 3
-  real *rTs = rfs + 27 * NT; // [3][NT] first Heun stage T*, row mod 3
+  real *rfs = ruy + 4 * NT;   // [3][9][NT] post-collision populations, row mod 3
+  real *rTs = rfs + 27 * NT;  // [3][NT] first Heun stage T*, row mod 3
+  const real third = real(1) / real(3), twelfth = real(1) / real(12);
+  const real big = sizeof(real) == 4 ? real(3.0e38) : real(1.0e300);
 
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * W;
@@ -119,25 +121,39 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
   const int yb = min(ya + H, P.ny);
   const int gx = x0 - 3 + t;
   const LineMap cm = map_line(gx, P.nx, P.hbc[0], P.hbc[1], 0);
+  const bool col_bnd = cm.src == 0 || cm.src == P.nx - 1;  // node may sit on an x boundary line
   const long long plane = P.plane;
   const real rho_bar = real(io.stats_in[0]);
+  // every row this CTA touches (ya-3 .. yb+2) is an interior row: no row mapping needed
+  const bool rows_simple = ya - 3 >= 1 && yb + 2 <= P.ny - 2;
   const bool xwall_strip = (P.hbc[0] == WALL && x0 - 3 < 0) || (P.hbc[1] == WALL && x0 + W + 3 > P.nx - 1);
   const bool xout_strip = (P.hbc[0] == OUTFLOW && x0 - 3 <= 0) || (P.hbc[1] == OUTFLOW && x0 + W + 3 >= P.nx - 1);
+  const bool any_outflow = P.hbc[0] == OUTFLOW || P.hbc[1] == OUTFLOW || P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
   const bool t_s2 = t >= 1 && t < NT - 1;
   const bool t_s3 = t >= 2 && t < NT - 2;
   const bool t_s4 = t >= 3 && t < NT - 3 && gx < P.nx && !cm.solid && !cm.outflow;
   const double wcol = line_weight(gx, P.nx, P.hbc[0], P.hbc[1]);
-  const real *fin = reinterpret_cast<const real *>(io.f_in);
-  const real *Tin = reinterpret_cast<const real *>(io.T_in);
+  const real *fin = reinterpret_cast<const real *>(io.f_in) + cm.src;
+  const real *Tin = reinterpret_cast<const real *>(io.T_in) + cm.src;
   real *fout = reinterpret_cast<real *>(io.f_out);
   real *Tout = reinterpret_cast<real *>(io.T_out);
   const int n_it = yb - ya + 6;  // rows ya-3 .. yb+2 pass through S1
   unsigned flags = 0;
   double acc = 0.0;
 
+  auto row_map = [&](int g) -> LineMap {
+    if (rows_simple) {
+      LineMap m;
+      m.src = g;
+      m.solid = 0;
+      m.wall = -1;
+      m.outflow = 0;
+      return m;
+    }
+    return map_line(g, P.ny, P.hbc[2], P.hbc[3], 2);
+  };
   auto stage_row = [&](int q, int slot) {
-    const LineMap rm = map_line(q, P.ny, P.hbc[2], P.hbc[3], 2);
-    const long long k = (long long)rm.src * P.nx + cm.src;
+    const long long k = (long long)row_map(q).src * P.nx;
     real *dst = stg + slot * 10 * NT + t;
 #pragma unroll
     for (int i = 0; i < 9; ++i) cp_async_real(dst + i * NT, fin + i * plane + k);
@@ -150,18 +166,21 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
     cp_async_commit();
   }
 
+  real c1jx = 0, c1jy = 0, n1jx = 0, n1jy = 0;  // S1 -> S2 (j of the row)
+  S3Carry<real> c2{}, n2{};
   S4Carry<real> cur{}, nxt{};
+  int f3 = 0;  // iq mod 3
   for (int iq = 0; iq < n_it; ++iq) {
     const int q = ya - 3 + iq;
     if (iq + PF < n_it) stage_row(q + PF, (iq + PF) % D);
     cp_async_commit();
     cp_async_wait<PF>();  // this thread's copies of row q have landed
     const int s4_0 = iq & 3, s4_1 = (iq + 3) & 3, s4_2 = (iq + 2) & 3, s4_3 = (iq + 1) & 3;  // rows q, q-1, q-2, q-3
-    const int f_r2 = (iq + 1) % 3, f_r3 = iq % 3, f_r4 = (iq + 2) % 3;  // f*/T* ring: rows q-2, q-3, q-4
+    const int f_r3 = f3, f_r2 = f3 == 2 ? 0 : f3 + 1, f_r4 = f3 == 0 ? 2 : f3 - 1;  // f*/T* rows q-3, q-2, q-4
 
     // ---- S1: row q ----
     {
-      const LineMap rm = map_line(q, P.ny, P.hbc[2], P.hbc[3], 2);
+      const LineMap rm = row_map(q);
       const real *st = stg + (iq % D) * 10 * NT + t;
       real f[9];
 #pragma unroll
@@ -179,21 +198,20 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
       rpsi[i0] = psi;
       rrho[i0] = rho;
       rT[i0] = Tt;
-      rjx[i0] = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-      rjy[i0] = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+      n1jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+      n1jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
     }
     __syncthreads();
 
     // ---- S2: row q-1 ----
     if (iq >= 2) {
       const int r = q - 1;
-      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      const LineMap rm = row_map(r);
       const int i0 = s4_1 * NT + t, iu = s4_0 * NT + t, id = s4_2 * NT + t;
       if (t_s2) {
         if (!cm.solid && !rm.solid) {
           const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
           const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
-          const real third = real(1) / real(3), twelfth = real(1) / real(12);
           real sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
           real sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
           const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
@@ -210,15 +228,18 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
           }
           const real psi_c = rpsi[i0];
           const real rho = rrho[i0];
-          const real fmx = -P.G * psi_c * sx, fmy = -P.G * psi_c * sy;
+          const real gps = -P.G * psi_c;
+          const real fmx = gps * sx, fmy = gps * sy;
           const real Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
           const real inv_rho = real(1) / rho;
-          const real ux = (rjx[i0] + real(0.5) * Fx) * inv_rho;
-          const real uy = (rjy[i0] + real(0.5) * Fy) * inv_rho;
+          const real ux = (c1jx + real(0.5) * Fx) * inv_rho;
+          const real uy = (c1jy + real(0.5) * Fy) * inv_rho;
           rux[i0] = ux;
           ruy[i0] = uy;
-          rfx[i0] = fmx;
-          rfy[i0] = fmy;
+          n2.fmx = fmx;
+          n2.fmy = fmy;
+          n2.fm2 = P.G * P.G * (sx * sx + sy * sy);  // |F^m|^2 / psi^2 (F^m is proportional to psi)
+          n2.inv_rho = inv_rho;
           if (ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
             rux[s4_3 * NT + t] = ux;
             ruy[s4_3 * NT + t] = -uy;
@@ -246,7 +267,7 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
     // ---- S3: row q-2 ----
     if (iq >= 4) {
       const int r = q - 2;
-      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      const LineMap rm = row_map(r);
       const int i0 = s4_2 * NT + t, iu = s4_1 * NT + t, id = s4_3 * NT + t;
       if (t_s3) {
         if (!cm.solid && !rm.solid) {
@@ -262,7 +283,6 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
           // Q (Eq. Q), solid links through psi_w (Eq. Q-psi-based)
           const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
           const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
-          const real third = real(1) / real(3), twelfth = real(1) / real(12);
           const real dsum = twelfth * (p5 + p6 + p7 + p8 - real(4) * psi_c);
           real qxx = third * (p1 + p3 - real(2) * psi_c) + dsum;
           real qyy = third * (p2 + p4 - real(2) * psi_c) + dsum;
@@ -282,14 +302,11 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
           qxx *= qf;
           qyy *= qf;
           qxy *= qf;
-          const real fmx = rfx[i0], fmy = rfy[i0];
           const real ux = rux[i0], uy = ruy[i0];
-          const real Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
-          const real inv_psi = real(1) / psi_c;
-          const real fm2 = (fmx * fmx + fmy * fmy) * (inv_psi * inv_psi);
+          const real Fx = c2.fmx + P.gx * (rho - rho_bar), Fy = c2.fmy + P.gy * (rho - rho_bar);
           real s_eta = P.s[7];
           if (P.var_eta) s_eta = real(1) / (real(3) * (P.eta_v + (P.eta_l - P.eta_v) * (rho - P.rho_v) * P.inv_drho) + real(0.5));
-          collide(P, fd, rho, delta, ux, uy, Fx, Fy, fm2, qxx, qyy, qxy, s_eta);
+          collide(P, fd, rho, delta, ux, uy, Fx, Fy, c2.fm2, qxx, qyy, qxy, s_eta);
           real *fs = rfs + f_r2 * 9 * NT + t;
 #pragma unroll
           for (int i = 0; i < 9; ++i) fs[i * NT] = fd[i];
@@ -298,11 +315,10 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
           if (ENERGY) {
             real Tw, Ts;
             const real T0 = rT[i0];
-            const real inv_rho = real(1) / rho;
             nxt.ux = ux;
             nxt.uy = uy;
             dpdT_parts(P, rho, &nxt.A, &nxt.B);
-            nxt.inv_rcv = inv_rho * P.cv_inv;
+            nxt.inv_rcv = c2.inv_rho * P.cv_inv;
             nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
             // frozen coefficients of Eq. (energy-equation): grad lambda = dlam grad rho, div u
             const real r1 = rrho[i0 + 1], r3 = rrho[i0 - 1], r2 = rrho[iu], r4 = rrho[id];
@@ -312,7 +328,8 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
             nxt.div = third * (rux[i0 + 1] - rux[i0 - 1]) +
                       twelfth * (rux[iu + 1] - rux[iu - 1] - rux[id - 1] + rux[id + 1]) +
                       third * (ruy[iu] - ruy[id]) + twelfth * (ruy[iu + 1] + ruy[iu - 1] - ruy[id - 1] - ruy[id + 1]);
-            if (t_fixed(P, cm.src, rm.src, &Tw)) {
+            const bool bnd = col_bnd || rm.src == 0 || rm.src == P.ny - 1;
+            if (bnd && t_fixed(P, cm.src, rm.src, &Tw)) {
               Ts = Tw - P.T_ref;
               nxt.k1 = real(0);
             } else if (rm.outflow) {
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
     // ---- S4: row q-3 ----
     if (iq >= 6 && t_s4) {
       const int r = q - 3;
-      const LineMap rm = map_line(r, P.ny, P.hbc[2], P.hbc[3], 2);
+      const LineMap rm = row_map(r);
       if (!rm.outflow) {
         // pull: f_i(x) = f*_i(x - c_i); ring rows r-1, r, r+1 are slots f_r4, f_r3, f_r2
         const real *lo = rfs + f_r4 * 9 * NT + t, *mid = rfs + f_r3 * 9 * NT + t, *hi = rfs + f_r2 * 9 * NT + t;
@@ -372,16 +389,15 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
         if (ws >= 0) zou_he(ws, fd, -real(0.5) * cur.Fx, -real(0.5) * cur.Fy);
         const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const real rho_new = P.rho_ref + delta;
-        const int i3 = s4_3 * NT + t;
-        real T_new = rT[i3];
+        real T_new = rT[s4_3 * NT + t];
         if (ENERGY) {
           real Tw;
-          if (!t_fixed(P, cm.src, rm.src, &Tw)) {
+          const bool bnd = col_bnd || rm.src == 0 || rm.src == P.ny - 1;
+          if (!(bnd && t_fixed(P, cm.src, rm.src, &Tw))) {
             const real *m0 = rTs + f_r3 * NT + t, *u0 = rTs + f_r2 * NT + t, *d0 = rTs + f_r4 * NT + t;
             const real c = m0[0];
             const real t1 = m0[1], t3 = m0[-1], t2 = u0[0], t4 = d0[0];
             const real t5 = u0[1], t6 = u0[-1], t7 = d0[-1], t8 = d0[1];
-            const real third = real(1) / real(3), twelfth = real(1) / real(12);
             const real gtx = third * (t1 - t3) + twelfth * (t5 - t6 - t7 + t8);
             const real gty = third * (t2 - t4) + twelfth * (t5 + t6 - t7 - t8);
             const real lap = (real(2) / real(3)) * (t1 + t2 + t3 + t4 - real(4) * c) +
@@ -395,12 +411,17 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
 #pragma unroll
         for (int i = 0; i < 9; ++i) fout[i * plane + k] = fd[i];
         Tout[k] = T_new;
-        if (!(rho_new == rho_new) || !(T_new == T_new) || isinf((double)rho_new) || isinf((double)T_new)) flags |= FLAG_NAN;
-        if (!(rho_new > real(0))) flags |= FLAG_RHO_NONPOS;
-        acc += wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]) * (double)rho_new;
+        if (!(fabs(T_new) <= big)) flags |= FLAG_NAN;
+        if (!(rho_new > real(0) && rho_new <= big)) flags |= (rho_new == rho_new ? FLAG_RHO_NONPOS : FLAG_NAN);
+        if (any_outflow) acc += wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]) * (double)rho_new;
+        else acc += (double)rho_new;
       }
     }
+    c1jx = n1jx;
+    c1jy = n1jy;
+    c2 = n2;
     cur = nxt;
+    f3 = f3 == 2 ? 0 : f3 + 1;
   }
   cp_async_wait<0>();
   if (flags) atomicOr(io.status, flags);

@@ -6,9 +6,9 @@
 namespace ppl_dev {
 
 constexpr int kNT32 = 128;  // threads (columns incl. the 3 + 3 halo) per CTA, FP32
-constexpr int kPF32 = 2;    // rows staged ahead, FP32
+constexpr int kPF32 = 1;    // rows staged ahead, FP32
 constexpr int kNT64 = 128;
-constexpr int kPF64 = 2;
+constexpr int kPF64 = 1;
 
 struct StepVariant {
   int nt;        // threads per CTA = strip width incl. halo
