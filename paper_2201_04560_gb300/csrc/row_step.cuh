@@ -99,11 +99,13 @@ constexpr size_t row_step_smem_bytes() {
   return (size_t)((PF + 3) * 10 + 5 * 4 + 27 + 3) * NT * sizeof(real);
 }
 
-template <typename real, bool ENERGY, int NT, int PF>
-__global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepIO io, const int H) {
+// SIMPLE: every row the CTA touches is an interior row (no wall, outflow or periodic
+// wrap in y), so all row classification folds away at compile time.
+template <typename real, bool ENERGY, int NT, int PF, bool SIMPLE>
+__device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io, const int H,
+                                         unsigned char *smem_raw) {
   constexpr int D = PF + 3;  // staging depth in rows
   constexpr int W = NT - 6;  // interior columns per strip
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   real *stg = reinterpret_cast<real *>(smem_raw);  // [D][10][NT]: f_0..f_8, T of staged rows
   real *rpsi = stg + D * 10 * NT;                   // rings [4][NT] indexed by row mod 4
   real *rrho = rpsi + 4 * NT;
@@ -124,8 +126,6 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
   const bool col_bnd = cm.src == 0 || cm.src == P.nx - 1;  // node may sit on an x boundary line
   const long long plane = P.plane;
   const real rho_bar = real(io.stats_in[0]);
-  // every row this CTA touches (ya-3 .. yb+2) is an interior row: no row mapping needed
-  const bool rows_simple = ya - 3 >= 1 && yb + 2 <= P.ny - 2;
   const bool xwall_strip = (P.hbc[0] == WALL && x0 - 3 < 0) || (P.hbc[1] == WALL && x0 + W + 3 > P.nx - 1);
   const bool xout_strip = (P.hbc[0] == OUTFLOW && x0 - 3 <= 0) || (P.hbc[1] == OUTFLOW && x0 + W + 3 >= P.nx - 1);
   const bool any_outflow = P.hbc[0] == OUTFLOW || P.hbc[1] == OUTFLOW || P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
@@ -140,9 +140,10 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
   const int n_it = yb - ya + 6;  // rows ya-3 .. yb+2 pass through S1
   unsigned flags = 0;
   double acc = 0.0;
+  real acc_s = real(0), acc_c = real(0);  // FP32 path: compensated per-thread sum
 
   auto row_map = [&](int g) -> LineMap {
-    if (rows_simple) {
+    if (SIMPLE) {
       LineMap m;
       m.src = g;
       m.solid = 0;
@@ -240,11 +241,11 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
           n2.fmy = fmy;
           n2.fm2 = P.G * P.G * (sx * sx + sy * sy);  // |F^m|^2 / psi^2 (F^m is proportional to psi)
           n2.inv_rho = inv_rho;
-          if (ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
+          if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
             rux[s4_3 * NT + t] = ux;
             ruy[s4_3 * NT + t] = -uy;
           }
-        } else if (ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny
+        } else if (!SIMPLE && ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny
           rux[i0] = rux[s4_3 * NT + t];
           ruy[i0] = -ruy[s4_3 * NT + t];
         }
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
             nxt.div = third * (rux[i0 + 1] - rux[i0 - 1]) +
                       twelfth * (rux[iu + 1] - rux[iu - 1] - rux[id - 1] + rux[id + 1]) +
                       third * (ruy[iu] - ruy[id]) + twelfth * (ruy[iu + 1] + ruy[iu - 1] - ruy[id - 1] - ruy[id + 1]);
-            const bool bnd = col_bnd || rm.src == 0 || rm.src == P.ny - 1;
+            const bool bnd = col_bnd || (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1));
             if (bnd && t_fixed(P, cm.src, rm.src, &Tw)) {
               Ts = Tw - P.T_ref;
               nxt.k1 = real(0);
@@ -348,9 +349,9 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
               Ts = T0 + k1;
             }
             rTs[f_r2 * NT + t] = Ts;
-            if (r == 1 && P.hbc[2] == WALL) rTs[f_r4 * NT + t] = Ts;  // mirror ghost of row -1
+            if (!SIMPLE && r == 1 && P.hbc[2] == WALL) rTs[f_r4 * NT + t] = Ts;  // mirror ghost of row -1
           }
-        } else if (ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {
+        } else if (!SIMPLE && ENERGY && rm.solid && r == P.ny && P.hbc[3] == WALL) {
           rTs[f_r2 * NT + t] = rTs[f_r4 * NT + t];  // mirror ghost of row ny (copy of row ny-2)
         }
       }
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
         real T_new = rT[s4_3 * NT + t];
         if (ENERGY) {
           real Tw;
-          const bool bnd = col_bnd || rm.src == 0 || rm.src == P.ny - 1;
+          const bool bnd = col_bnd || (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1));
           if (!(bnd && t_fixed(P, cm.src, rm.src, &Tw))) {
             const real *m0 = rTs + f_r3 * NT + t, *u0 = rTs + f_r2 * NT + t, *d0 = rTs + f_r4 * NT + t;
             const real c = m0[0];
@@ -411,10 +412,19 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
 #pragma unroll
         for (int i = 0; i < 9; ++i) fout[i * plane + k] = fd[i];
         Tout[k] = T_new;
-        if (!(fabs(T_new) <= big)) flags |= FLAG_NAN;
-        if (!(rho_new > real(0) && rho_new <= big)) flags |= (rho_new == rho_new ? FLAG_RHO_NONPOS : FLAG_NAN);
-        if (any_outflow) acc += wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]) * (double)rho_new;
-        else acc += (double)rho_new;
+        if (!(rho_new > real(0) && rho_new <= big && fabs(T_new) <= big))
+          flags |= (rho_new == rho_new && fabs(T_new) <= big && rho_new <= big) ? FLAG_RHO_NONPOS : FLAG_NAN;
+        const real wr = (!SIMPLE && any_outflow) ? real(wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]))
+                                                 : (any_outflow ? real(wcol) : real(1));
+        if (sizeof(real) == 8) {
+          acc += double(wr * rho_new);
+        } else {
+          // compensated FP32 sum of this thread's column (FP64 beyond the thread)
+          const real yk = wr * rho_new - acc_c;
+          const real tk = acc_s + yk;
+          acc_c = (tk - acc_s) - yk;
+          acc_s = tk;
+        }
       }
     }
     c1jx = n1jx;
@@ -424,6 +434,7 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
     f3 = f3 == 2 ? 0 : f3 + 1;
   }
   cp_async_wait<0>();
+  if (sizeof(real) == 4) acc = double(acc_s) - double(acc_c);
   if (flags) atomicOr(io.status, flags);
 
   // ---- deterministic FP64 reduction of sum rho^{n+1} ----
@@ -461,6 +472,18 @@ __global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepI
       *io.counter = 0u;
     }
   }
+}
+
+
+template <typename real, bool ENERGY, int NT, int PF>
+__global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepIO io, const int H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ya = blockIdx.y * H;
+  const int yb = min(ya + H, P.ny);
+  if (ya - 3 >= 1 && yb + 2 <= P.ny - 2)
+    row_body<real, ENERGY, NT, PF, true>(P, io, H, smem_raw);
+  else
+    row_body<real, ENERGY, NT, PF, false>(P, io, H, smem_raw);
 }
 
 }  // namespace ppl_dev
