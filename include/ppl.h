@@ -181,6 +181,39 @@ int64_t ppl_launch_count(const ppl_t *h);
 /* Release the handle and its device memory (NULL is ignored). */
 void ppl_destroy(ppl_t *h);
 
+/*
+ * One time step on caller-owned device buffers, with no device memory allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- host applications or plugins whose framework owns and pre-plans every
+ * device allocation, and latency-critical loops where an allocation's implicit device
+ * synchronisation is not acceptable. It runs the same fused step kernel as ppl_step.
+ *
+ *  cfg        configuration as for ppl_init; energy_on selects whether T is advanced in
+ *             this step (iso_steps is not used). Per-boundary-node arrays (rho_w, T_w,
+ *             T_dirichlet) are not supported here: they would need device copies.
+ *  f_in, T_in    device state in: populations [9][ny][nx] and T [ny][nx], doubles for
+ *             PPL_FP64, floats holding f_i - w_i rho_ref and T - T_ref for PPL_FP32DEV
+ *  f_out, T_out  device state out, same layout; must not alias the inputs
+ *  stats_in   device double[1]: rho_bar (mean density) of the input state
+ *  stats_out  device double[2]: rho_bar and total mass of the output state
+ *  status     device uint32: PPL_FLAG_* bits are OR-ed in (the caller clears it)
+ *  cuda_stream   stream to enqueue on (NULL: legacy default stream); nothing synchronises
+ *
+ * Scratch: the FP64 per-CTA partials of the mass reduction and a completion counter live
+ * in a static device array of the library (4096 partials, 32 KB), held by every GPU that
+ * loads the library until the process exits. A grid that needs more than 4096 CTAs
+ * (about nx > 4096 * 122 columns, or more rows per column strip than one wave of CTAs
+ * covers) is rejected with PPL_E_INVAL before anything runs. The first call on each device
+ * resolves the scratch's device address and sets kernel attributes; make that first call
+ * before any stream capture. All calls share the one scratch array and it keeps the last
+ * call's contents (the counter is cleared by each call): calls that overlap on the GPU,
+ * on different streams or threads, race and must be serialised by the caller.
+ * Returns PPL_OK, PPL_E_INVAL (bad arguments, unsupported per-node arrays, too large a
+ * grid) or PPL_E_CUDA.
+ */
+int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, void *f_out, void *T_out,
+                     const double *stats_in, double *stats_out, uint32_t *status, void *cuda_stream);
+
 /* Static description of a return code. */
 const char *ppl_strerror(int code);
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -894,6 +895,106 @@ int ppl_load(ppl_t *h, const char *path) {
 }
 
 int64_t ppl_launch_count(const ppl_t *h) { return h ? h->launches : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// ppl_step_noalloc: one fused step on caller-owned device buffers, allocating nothing.
+// Its scratch (per-CTA FP64 partials of the mass sum and the CTA completion counter)
+// lives in the file-scope array below, which every GPU that loads the library holds
+// until the process exits.
+// ---------------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxCtas = 4096;  // CTA partials the static scratch can hold
+// [0, kNoAllocMaxCtas): CTA partials; [kNoAllocMaxCtas]: completion counter (as unsigned)
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxCtas + 1];
+
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_scratch per device
+
+// one-time set-up on the current device: the device address of the scratch (the host-side
+// name of a __device__ array is not a device address) and the kernels' shared-memory limit
+int noalloc_setup(double **scratch) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return PPL_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    for (const StepVariant &v : {step_variant_fp64(), step_variant_fp32()})
+      for (int e = 0; e < 2; ++e)
+        CK(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+    g_noalloc_addr[dev] = p;
+  }
+  *scratch = (double *)g_noalloc_addr[dev];
+  return PPL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, void *f_out, void *T_out,
+                     const double *stats_in, double *stats_out, uint32_t *status, void *cuda_stream) {
+  int rc = validate(cfg);
+  if (rc) return rc;
+  if (!f_in || !T_in || !f_out || !T_out || !stats_in || !stats_out || !status) return PPL_E_INVAL;
+  if (f_in == f_out || T_in == T_out) return PPL_E_INVAL;  // the step reads neighbours of what it writes
+  for (int s = 0; s < 4; ++s)
+    if (cfg->rho_w[s] || cfg->T_w[s] || cfg->T_dirichlet[s]) return PPL_E_INVAL;  // would need device copies
+  double *scratch = nullptr;
+  rc = noalloc_setup(&scratch);
+  if (rc) return rc;
+  const StepVariant var = cfg->precision == PPL_FP64 ? step_variant_fp64() : step_variant_fp32();
+  // the launch shape of ppl_init: strips of (nt - 6) columns, one wave of CTAs over the rows
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, var.fn[1], var.nt, var.smem));
+  const int slots = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const int strips = (cfg->nx + (var.nt - 6) - 1) / (var.nt - 6);
+  int yblocks = slots / strips;
+  if (yblocks < 1) yblocks = 1;
+  int H = (cfg->ny + yblocks - 1) / yblocks;
+  if (H < 8) H = 8;
+  const dim3 grid(strips, (cfg->ny + H - 1) / H);
+  if ((long long)grid.x * grid.y > kNoAllocMaxCtas) return PPL_E_INVAL;  // beyond the static scratch
+  // parameters of this configuration (a stack handle carries no device memory)
+  ppl_sim tmp;
+  tmp.cfg = *cfg;
+  tmp.prec = cfg->precision;
+  const void *none[4] = {nullptr, nullptr, nullptr, nullptr};
+  const uint8_t *none8[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  unsigned *counter = (unsigned *)(scratch + kNoAllocMaxCtas);
+  CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));  // the finalize relies on a zero counter
+  StepIO io;
+  io.f_in = f_in;
+  io.T_in = T_in;
+  io.f_out = f_out;
+  io.T_out = T_out;
+  io.stats_in = stats_in;
+  io.stats_out = stats_out;
+  io.partials = scratch;
+  io.counter = counter;
+  io.status = status;
+  const int e = cfg->energy_on ? 1 : 0;
+  if (cfg->precision == PPL_FP64) {
+    Params<double> P;
+    fill_params<double>(&tmp, P, (const double *const *)none, (const double *const *)none, none8);
+    void *args[] = {(void *)&P, (void *)&io, (void *)&H};
+    CK(cudaLaunchKernel(var.fn[e], grid, dim3(var.nt), args, var.smem, stream));
+  } else {
+    Params<float> P;
+    fill_params<float>(&tmp, P, (const float *const *)none, (const float *const *)none, none8);
+    void *args[] = {(void *)&P, (void *)&io, (void *)&H};
+    CK(cudaLaunchKernel(var.fn[e], grid, dim3(var.nt), args, var.smem, stream));
+  }
+  return PPL_OK;
+}
 
 void ppl_destroy(ppl_t *h) {
   if (!h) return;

@@ -98,6 +98,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_tc.argtypes = [_D, _D, _D]
     L.ppl_tc.restype = _D
     L.ppl_maxwell.argtypes = [_D, _D, _D, _D, _D, _PD, _PD, _PD]
+    L.ppl_step_noalloc.argtypes = [ctypes.POINTER(PplConfig)] + [ctypes.c_void_p] * 8
+    L.ppl_step_noalloc.restype = ctypes.c_int
     L.ppl_refine_a.argtypes = [_D, ctypes.c_int32, ctypes.c_int32]
     L.ppl_refine_a.restype = _D
     for name in ("ppl_init", "ppl_reset", "ppl_set_stream", "ppl_step", "ppl_step_async", "ppl_sync",
@@ -166,6 +168,15 @@ def make_config(cfg: dict):
     C.contact_model = 0
     C.G_w = float(cfg.get("G_w", 0.0))
     return C, keep
+
+
+def step_noalloc(cfg: dict, f_in, T_in, f_out, T_out, stats_in, stats_out, status, stream=None) -> int:
+    """ppl_step_noalloc on caller-owned device buffers (integer device addresses, e.g.
+    torch data_ptr()s): one step that allocates no device memory. Returns the ppl code."""
+    C, keep = make_config(cfg)
+    handle = getattr(stream, "cuda_stream", stream)
+    ptrs = [ctypes.c_void_p(int(p)) for p in (f_in, T_in, f_out, T_out, stats_in, stats_out, status)]
+    return load_library().ppl_step_noalloc(ctypes.byref(C), *ptrs, ctypes.c_void_p(handle or None))
 
 
 class Simulation:
