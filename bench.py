@@ -96,6 +96,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_traffic():
+    """ncu DRAM bytes of one FP32 step launch at the bench size, if taken on the current kernel sources."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        return rec["traffic_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -267,7 +282,7 @@ def main():
                    "grid": [NX, NY], "l2": "state (335 MB FP32, 671 MB FP64 per buffer) larger than L2",
                    "parallelism": "replica per GPU" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
-                     "traffic": None, "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
+                     "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,
                  "roofline": {"bound": "alu", "achieved_gbs": ach64, "hbm_frac": ach64 / hbm,
                               "bytes_per_node": BYTES_PER_NODE["fp64"]}},

@@ -88,6 +88,7 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename real>
 struct S3Carry {  // S2 (row r) -> S3 (row r, next iteration)
   real fmx, fmy, fm2, inv_rho;  // F^m, |F^m|^2 / psi^2 = G^2 |s|^2, 1/rho
+  real qxx, qyy, qxy;           // Q of Eq. (Q)
 };
 template <typename real>
 struct S4Carry {  // S3 (row r) -> S4 (row r, next iteration)
@@ -96,7 +97,7 @@ struct S4Carry {  // S3 (row r) -> S4 (row r, next iteration)
 
 template <int NT, int PF, typename real>
 constexpr size_t row_step_smem_bytes() {
-  return (size_t)((PF + 3) * 10 + 5 * 4 + 27 + 3) * NT * sizeof(real);
+  return (size_t)((PF + 3) * 10 + 5 * 4 + 18 + 3) * NT * sizeof(real);
 }
 
 // SIMPLE: every row the CTA touches is an interior row (no wall, outflow or periodic
@@ -112,8 +113,10 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   real *rT = rrho + 4 * NT;
   real *rux = rT + 4 * NT;
   real *ruy = rux + 4 * NT;
-  real *rfs = ruy + 4 * NT;   // [3][9][NT] post-collision populations, row mod 3
-  real *rTs = rfs + 27 * NT;  // [3][NT] first Heun stage T*, row mod 3
+  // [3][6][NT] post-collision populations that stream sideways (c_x != 0: i = 1, 3, 5, 6,
+  // 7, 8), row mod 3; f*_0, f*_2, f*_4 stay in the column and are handed over in registers
+  real *rfs = ruy + 4 * NT;
+  real *rTs = rfs + 18 * NT;  // [3][NT] first Heun stage T*, row mod 3
   const real third = real(1) / real(3), twelfth = real(1) / real(12);
   const real big = sizeof(real) == 4 ? real(3.0e38) : real(1.0e300);
 
@@ -168,6 +171,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   }
 
   real c1jx = 0, c1jy = 0, n1jx = 0, n1jy = 0;  // S1 -> S2 (j of the row)
+  real f0n = 0, f2n = 0, f4n = 0, f0c = 0, f2c1 = 0, f2c2 = 0;  // column-bound f* (S3 -> S4)
   S3Carry<real> c2{}, n2{};
   S4Carry<real> cur{}, nxt{};
   int f3 = 0;  // iq mod 3
@@ -215,19 +219,37 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
           const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
           real sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
           real sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
+          const real psi_c = rpsi[i0];
+          // Q (Eq. Q) from the same psi neighbourhood
+          const real dsum = twelfth * (p5 + p6 + p7 + p8 - real(4) * psi_c);
+          real qxx = third * (p1 + p3 - real(2) * psi_c) + dsum;
+          real qyy = third * (p2 + p4 - real(2) * psi_c) + dsum;
+          const real qxy = twelfth * (p5 - p6 + p7 - p8);
           const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
           if (ws >= 0) {
-            // solid links (psi = 0 in the ring) carry psi_w = psi(rho_w, T); their weights
-            // sum to 1/2 along the outward normal
+            // solid links (psi = 0 in the ring) carry psi_w = psi(rho_w, T) (Eqs. shanchen-walls,
+            // psi-based-formula, Q-psi-based): their force weights sum to 1/2 along the outward
+            // normal; in Q they add (1/2, 1/6) psi_w to the normal and tangential components
             const real argw = psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]);
             if (!(argw >= real(0))) flags |= FLAG_PSI_NEG;
-            const real hw = real(0.5) * sqrt(fmax(argw, real(0)));
+            const real psi_w = sqrt(fmax(argw, real(0)));
+            const real hw = real(0.5) * psi_w;
             if (ws == 0) sx -= hw;
             else if (ws == 1) sx += hw;
             else if (ws == 2) sy -= hw;
             else sy += hw;
+            if (ws < 2) {
+              qxx += hw;
+              qyy += (real(1) / real(6)) * psi_w;
+            } else {
+              qxx += (real(1) / real(6)) * psi_w;
+              qyy += hw;
+            }
           }
-          const real psi_c = rpsi[i0];
+          const real qf = P.kappa_G2 * psi_c;
+          n2.qxx = qf * qxx;
+          n2.qyy = qf * qyy;
+          n2.qxy = qf * qxy;
           const real rho = rrho[i0];
           const real gps = -P.G * psi_c;
           const real fmx = gps * sx, fmy = gps * sy;
@@ -280,37 +302,21 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
           // rounded to the precision of rho)
           const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
           const real rho = rrho[i0];
-          const real psi_c = rpsi[i0];
-          // Q (Eq. Q), solid links through psi_w (Eq. Q-psi-based)
-          const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
-          const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
-          const real dsum = twelfth * (p5 + p6 + p7 + p8 - real(4) * psi_c);
-          real qxx = third * (p1 + p3 - real(2) * psi_c) + dsum;
-          real qyy = third * (p2 + p4 - real(2) * psi_c) + dsum;
-          real qxy = twelfth * (p5 - p6 + p7 - p8);
-          const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
-          if (ws >= 0) {
-            const real psi_w = sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]), real(0)));
-            if (ws < 2) {
-              qxx += real(0.5) * psi_w;
-              qyy += (real(1) / real(6)) * psi_w;
-            } else {
-              qxx += (real(1) / real(6)) * psi_w;
-              qyy += real(0.5) * psi_w;
-            }
-          }
-          const real qf = P.kappa_G2 * psi_c;
-          qxx *= qf;
-          qyy *= qf;
-          qxy *= qf;
           const real ux = rux[i0], uy = ruy[i0];
           const real Fx = c2.fmx + P.gx * (rho - rho_bar), Fy = c2.fmy + P.gy * (rho - rho_bar);
           real s_eta = P.s[7];
           if (P.var_eta) s_eta = real(1) / (real(3) * (P.eta_v + (P.eta_l - P.eta_v) * (rho - P.rho_v) * P.inv_drho) + real(0.5));
-          collide(P, fd, rho, delta, ux, uy, Fx, Fy, c2.fm2, qxx, qyy, qxy, s_eta);
-          real *fs = rfs + f_r2 * 9 * NT + t;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) fs[i * NT] = fd[i];
+          collide(P, fd, rho, delta, ux, uy, Fx, Fy, c2.fm2, c2.qxx, c2.qyy, c2.qxy, s_eta);
+          real *fs = rfs + f_r2 * 6 * NT + t;
+          fs[0 * NT] = fd[1];
+          fs[1 * NT] = fd[3];
+          fs[2 * NT] = fd[5];
+          fs[3 * NT] = fd[6];
+          fs[4 * NT] = fd[7];
+          fs[5 * NT] = fd[8];
+          f0n = fd[0];
+          f2n = fd[2];
+          f4n = fd[4];
           nxt.Fx = Fx;
           nxt.Fy = Fy;
           if (ENERGY) {
@@ -375,17 +381,17 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
       const LineMap rm = row_map(r);
       if (!rm.outflow) {
         // pull: f_i(x) = f*_i(x - c_i); ring rows r-1, r, r+1 are slots f_r4, f_r3, f_r2
-        const real *lo = rfs + f_r4 * 9 * NT + t, *mid = rfs + f_r3 * 9 * NT + t, *hi = rfs + f_r2 * 9 * NT + t;
+        const real *lo = rfs + f_r4 * 6 * NT + t, *mid = rfs + f_r3 * 6 * NT + t, *hi = rfs + f_r2 * 6 * NT + t;
         real fd[9];
-        fd[0] = mid[0];
-        fd[1] = mid[1 * NT - 1];
-        fd[2] = lo[2 * NT];
-        fd[3] = mid[3 * NT + 1];
-        fd[4] = hi[4 * NT];
-        fd[5] = lo[5 * NT - 1];
-        fd[6] = lo[6 * NT + 1];
-        fd[7] = hi[7 * NT + 1];
-        fd[8] = hi[8 * NT - 1];
+        fd[0] = f0c;       // f*_0 of row r (previous iteration's S3)
+        fd[1] = mid[0 * NT - 1];
+        fd[2] = f2c2;      // f*_2 of row r-1 (two iterations back)
+        fd[3] = mid[1 * NT + 1];
+        fd[4] = f4n;       // f*_4 of row r+1 (this iteration's S3)
+        fd[5] = lo[2 * NT - 1];
+        fd[6] = lo[3 * NT + 1];
+        fd[7] = hi[4 * NT + 1];
+        fd[8] = hi[5 * NT - 1];
         const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
         if (ws >= 0) zou_he(ws, fd, -real(0.5) * cur.Fx, -real(0.5) * cur.Fy);
         const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
@@ -431,6 +437,9 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
     c1jy = n1jy;
     c2 = n2;
     cur = nxt;
+    f0c = f0n;
+    f2c2 = f2c1;
+    f2c1 = f2n;
     f3 = f3 == 2 ? 0 : f3 + 1;
   }
   cp_async_wait<0>();
@@ -475,8 +484,10 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
 }
 
 
+// FP32: 5 CTAs per SM fit in shared memory; ask the register allocator for the same
 template <typename real, bool ENERGY, int NT, int PF>
-__global__ void __launch_bounds__(NT) row_step(const Params<real> P, const StepIO io, const int H) {
+__global__ void __launch_bounds__(NT, sizeof(real) == 4 ? 5 : 1) row_step(const Params<real> P, const StepIO io,
+                                                                       const int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ya = blockIdx.y * H;
   const int yb = min(ya + H, P.ny);
