@@ -82,6 +82,8 @@ typedef struct {
   const double *rho_w[4];       /* optional per-boundary-node wall density */
   const double *T_w[4];         /* optional per-boundary-node Dirichlet value */
   const uint8_t *T_dirichlet[4]; /* optional per-boundary-node kind: 1 Dirichlet, 0 adiabatic */
+  double rho_bar_fixed; /* finite: the domain-mean density of Eq. (gravitational_force) is given
+                           (the grid is a window of a larger domain); NaN: mean over this grid */
 } orc_params;
 
 /* M^-1 = M^T diag(1/|row_k|^2): rows of M are orthogonal */
@@ -336,7 +338,7 @@ static long macro(const orc_params *P, const double *f, const double *T, work_t 
   /* rho_bar: spatial mean over the whole domain (Eq. gravitational_force) */
   double sr = 0.0;
   for (size_t k = 0; k < N; ++k) sr += w->rho[k];
-  *rho_bar = sr / (double)N;
+  *rho_bar = isnan(P->rho_bar_fixed) ? sr / (double)N : P->rho_bar_fixed;
   /* 2. psi (Eq. psi) */
   for (size_t k = 0; k < N; ++k)
     if (pr_psi(P, w->rho[k], T[k], &w->psi[k])) return 2 + (long)k;

@@ -35,6 +35,7 @@ class OrcParams(ctypes.Structure):
         ("hydro_bc", ctypes.c_int32 * 4), ("thermal_bc", ctypes.c_int32 * 4),
         ("T_side", _D * 4), ("rho_w_side", _D * 4),
         ("rho_w", _PD * 4), ("T_w", _PD * 4), ("T_dirichlet", _PU8 * 4),
+        ("rho_bar_fixed", _D),
     ]
 
 
@@ -87,6 +88,7 @@ def make_params(cfg: dict):
         setattr(P, k, float(cfg[k]))
     for i in range(9):
         P.s[i] = float(cfg["s"][i])
+    P.rho_bar_fixed = float(cfg.get("rho_bar_fixed", float("nan")))
     P.energy_on = int(cfg["energy_on"])
     P.iso_steps = int(cfg["iso_steps"])
     for sd in range(4):
@@ -136,6 +138,39 @@ class Oracle:
         if err:
             raise FloatingPointError("oracle fields failed (code %d)" % err)
         return {"rho": rho, "ux": ux, "uy": uy, "T": self.T.copy(), "rho_bar": rb.value}
+
+
+def window_step(cfg: dict, fields, x0: int, x1: int, y0: int, y1: int, rho_bar: float, steps: int = 1):
+    """Advance a window [y0, y1) x [x0, x1) of a larger domain by `steps` steps.
+
+    The window is padded by 3 * steps nodes on every side that is open (not a domain
+    wall); padded columns/rows wrap around the periodic axes of the domain. The domain-mean
+    density is given (rho_bar, Eq. gravitational_force). Returns (f, T) of the window
+    itself, whose nodes are exact: each depends only on inputs within 3 * steps nodes.
+    fields: (rho0, ux0, uy0, T0) of the whole domain."""
+    ny, nx = np.asarray(fields[0]).shape
+    pad = 3 * int(steps)
+    xs = np.arange(x0 - pad, x1 + pad)
+    ylo = 0 if (cfg["hydro_bc"][2] != 0 and y0 - pad <= 0) else y0 - pad
+    yhi = ny if (cfg["hydro_bc"][3] != 0 and y1 + pad >= ny) else y1 + pad
+    ys = np.arange(ylo, yhi)
+    if cfg["hydro_bc"][0] != 0:
+        raise ValueError("window_step expects a domain periodic in x")
+    wcfg = dict(cfg)
+    wcfg["nx"], wcfg["ny"] = len(xs), len(ys)
+    wcfg["rho_bar_fixed"] = float(rho_bar)
+    hb, tb = list(cfg["hydro_bc"]), list(cfg["thermal_bc"])
+    wcfg["hydro_bc"] = [0, 0, hb[2] if ylo == 0 else 0, hb[3] if yhi == ny else 0]
+    wcfg["thermal_bc"] = [0, 0, tb[2] if ylo == 0 else 0, tb[3] if yhi == ny else 0]
+    for name in ("rho_w", "T_w", "T_dirichlet"):
+        arrs = list(cfg.get(name) or [None] * 4)
+        wcfg[name] = [None, None] + [None if a is None else np.asarray(a)[np.mod(xs, nx)] for a in arrs[2:]]
+    sub = [np.asarray(a)[np.ix_(np.mod(ys, ny), np.mod(xs, nx))] for a in fields]
+    o = Oracle(wcfg, *sub)
+    o.step(steps)
+    iy = slice(y0 - ylo, y1 - ylo)
+    ix = slice(pad, pad + (x1 - x0))
+    return o.f[:, iy, ix].copy(), o.T[iy, ix].copy()
 
 
 def energy_rhs(cfg: dict, rho, ux, uy, T):

@@ -302,3 +302,20 @@ def test_wall_film_reaches_no_slip_rest(pr08):
     assert np.abs(fl["uy"]).max() < 1e-5
     assert np.abs(fl["ux"]).max() < 1e-12
     assert fl["rho"][:, 0].max() == pytest.approx(rl, rel=0.05)
+
+
+@pytest.mark.parametrize("steps,g", [(1, 3e-5), (2, 0.0)])
+def test_window_step_reproduces_the_full_domain(steps, g):
+    # A window padded by 3 nodes per step on its open sides depends on nothing outside the
+    # padding, so its nodes equal those of the whole-domain step (rho_bar given).
+    e = thermo.PR()
+    rv, rl, _ = thermo.maxwell(e, 0.86 * e.Tc)
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=40, ny=36, g=g, g_ref_height=36)
+    full = oracle.Oracle(cfg, *ic)
+    full.step(steps)
+    rbar = float(np.mean(ic[0]))
+    for (x0, x1, y0, y1) in [(0, 12, 0, 9), (30, 40, 5, 20), (14, 26, 28, 36), (35, 45, 10, 14)]:
+        f, T = oracle.window_step(cfg, ic, x0, x1, y0, y1, rbar, steps=steps)
+        xs = np.arange(x0, x1) % 40
+        np.testing.assert_allclose(f, full.f[:, y0:y1][:, :, xs], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(T, full.T[y0:y1][:, xs], rtol=1e-12, atol=0)
