@@ -231,6 +231,31 @@ int ppl_maxwell(double a, double b, double R, double omega, double T, double *rh
 /* Eq. (a-deltax): a on a mesh of n nodes per length, from a_base on n_base nodes. */
 double ppl_refine_a(double a_base, int32_t n_base, int32_t n);
 
+/* Sec. 3.2 step 2: the sigma for which the mechanical-stability coexistence of Eq.
+ * (integral_coexistence_curve) lands on the Maxwell densities at temperature T (secant
+ * started at -16 G sigma_0 = 2). PPL_E_INVAL for T >= T_c, bad parameters or no convergence. */
+int ppl_sigma_for(double a, double b, double R, double omega, double G, double T, double *sigma);
+
+/* Planar surface tension of Eq. (surface_tension) at (T, sigma, kappa): the profile solves the
+ * constant normal stress of the Sec. 2.1 pressure tensor (the (1 - kappa) term read as
+ * psi grad grad psi) between the mechanical-stability coexistence densities. */
+int ppl_gamma_planar(double a, double b, double R, double omega, double G, double T, double sigma, double kappa,
+                     double *gamma);
+
+/* Sec. 3.2 step 3, Eq. (gamma-meshes-relation) with 0 = the base mesh: the kappa of a mesh
+ * with n nodes per length such that gamma scales with dx (gamma_n = gamma_base n_base / n);
+ * a follows Eq. (a-deltax), sigma is tuned on each mesh, T = T_ratio T_c on each mesh. */
+int ppl_kappa_for(double a_base, int32_t n_base, int32_t n, double b, double R, double omega, double G,
+                  double T_ratio, double kappa_base, double *kappa);
+
+/* The refinement procedure of Sec. 3 applied to a configuration: grid x n/n_base; a per
+ * Eq. (a-deltax); temperatures (T_side, T_ref) with T_c (~ dx^2); gravity ~ dx^3 (Table 1);
+ * sigma tuned at T_ratio T_c; kappa per Eq. (gamma-meshes-relation). lambda, c_v, eta, rho_w
+ * and the MRT rates are O(1) and kept. The time step scales as dx^2: one base step is
+ * (n / n_base)^2 refined steps. Per-boundary-node arrays must be rebuilt by the caller
+ * (PPL_E_INVAL if base has any). */
+int ppl_refine(const ppl_config *base, int32_t n_base, int32_t n, double T_ratio, ppl_config *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -186,28 +186,33 @@ def planar_gamma(eos: PR, T: float, sigma: float, kappa: float):
     """Planar surface tension, Sec. 3.2 Eq. (surface_tension).
 
     The planar normal stress of the Sec. 2.1 pressure tensor (reading: the (1-kappa)
-    term is psi grad grad psi) is P_xx = p_EOS + 2 sigma G^2 psi'^2 + (G/4) psi psi''
-    (c = 1), constant across the interface. With Y(psi) = (d psi/dx)^2 it is the linear
-    ODE  dY/dpsi + (16 G sigma / psi) Y = (8/(G psi)) (p0 - p_EOS), whose solution
-    vanishing in the vapour bulk gives d psi/dx = sqrt(Y). Then
-    gamma = (G/6)(1-kappa) int psi psi'' dx = -(G/6)(1-kappa) int sqrt(Y) d psi.
+    term is psi grad grad psi) is P_xx = p_EOS + 2 sigma G^2 psi_x^2 + (G/4) psi psi_xx
+    (c = 1), constant (= p0) across the interface. Multiplying by (8/(G psi)) psi_x psi^e,
+    e = 16 G sigma, gives the first integral d(Y psi^e) = (8/(G psi)) (p0 - p_EOS) psi^e d psi
+    with Y = psi_x^2, vanishing in both bulks. psi(rho) is not monotone near the liquid
+    bulk, so the profile is parametrised by rho (d psi = psi'(rho) d rho) and Y psi^e is
+    accumulated from the nearer bulk. Then
+    gamma = (G/6)(1-kappa) int psi psi_xx dx = -(G/6)(1-kappa) int sqrt(Y) |psi'| d rho.
     """
     rv, rl, p0 = mechanical_coexistence(eos, T, sigma)
     G = eos.G
-    psi_v, psi_l = float(eos.psi(rv, T)), float(eos.psi(rl, T))
-    # rho(psi) inverse on [rho_v, rho_l] (psi is monotone there)
-    def rho_of(ps):
-        return optimize.brentq(lambda r: float(eos.psi(r, T)) - ps, rv * (1 - 1e-12), rl * (1 + 1e-12),
-                               xtol=1e-15)
-    e = 16.0 * G * sigma  # integrating factor psi^{e}
+    e = 16.0 * G * sigma
+    rmid = 0.5 * (rv + rl)
 
-    def Y(ps):
-        inner, _ = integrate.quad(
-            lambda q: (8.0 / (G * q)) * (p0 - float(eos.p(rho_of(q), T))) * q ** e,
-            psi_v, ps, epsabs=1e-14, epsrel=1e-11, limit=200)
-        return max(inner, 0.0) * ps ** (-e)
+    def src(r):  # d(Y psi^e)/d rho along the profile
+        ps = float(eos.psi(r, T))
+        return (8.0 / (G * ps)) * (p0 - float(eos.p(r, T))) * ps ** e * float(dpsi_drho(eos, r, T))
 
-    val, _ = integrate.quad(lambda q: math.sqrt(Y(q)), psi_v, psi_l, epsabs=1e-12, epsrel=1e-9, limit=200)
+    def Y(r):
+        if r <= rmid:
+            ye, _ = integrate.quad(src, rv, r, epsabs=1e-14, epsrel=1e-11, limit=200)
+        else:
+            ye, _ = integrate.quad(src, r, rl, epsabs=1e-14, epsrel=1e-11, limit=200)
+            ye = -ye
+        return max(ye, 0.0) * float(eos.psi(r, T)) ** (-e)
+
+    val, _ = integrate.quad(lambda r: math.sqrt(Y(r)) * abs(float(dpsi_drho(eos, r, T))), rv, rl,
+                            points=[rmid], epsabs=1e-12, epsrel=1e-9, limit=200)
     return -(G / 6.0) * (1.0 - kappa) * val
 
 

@@ -14,6 +14,7 @@ LIB = os.path.join(BUILD, "libppl.so")
 # square root (its error is budgeted against the FP64 oracle), the FP64 step is IEEE
 UNITS = {
     "ppl.cu": [],
+    "thermo.cu": [],
     "step_fp64.cu": [],
     "step_fp32.cu": ["--use_fast_math"],
 }

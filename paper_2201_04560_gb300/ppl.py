@@ -100,6 +100,12 @@ def load_library(build_if_missing: bool = True):
     L.ppl_maxwell.argtypes = [_D, _D, _D, _D, _D, _PD, _PD, _PD]
     L.ppl_step_noalloc.argtypes = [ctypes.POINTER(PplConfig)] + [ctypes.c_void_p] * 8
     L.ppl_step_noalloc.restype = ctypes.c_int
+    L.ppl_sigma_for.argtypes = [_D] * 6 + [_PD]
+    L.ppl_gamma_planar.argtypes = [_D] * 8 + [_PD]
+    L.ppl_kappa_for.argtypes = [_D, ctypes.c_int32, ctypes.c_int32] + [_D] * 6 + [_PD]
+    L.ppl_refine.argtypes = [ctypes.POINTER(PplConfig), ctypes.c_int32, ctypes.c_int32, _D, ctypes.POINTER(PplConfig)]
+    for name in ("ppl_sigma_for", "ppl_gamma_planar", "ppl_kappa_for", "ppl_refine"):
+        getattr(L, name).restype = ctypes.c_int
     L.ppl_refine_a.argtypes = [_D, ctypes.c_int32, ctypes.c_int32]
     L.ppl_refine_a.restype = _D
     for name in ("ppl_init", "ppl_reset", "ppl_set_stream", "ppl_step", "ppl_step_async", "ppl_sync",
@@ -130,6 +136,40 @@ def maxwell(a: float, b: float, R: float, omega: float, T: float):
 
 def refine_a(a_base: float, n_base: int, n: int) -> float:
     return load_library().ppl_refine_a(a_base, n_base, n)
+
+
+def sigma_for(a, b, R, omega, G, T) -> float:
+    """Sec. 3.2 sigma tuning (ppl_sigma_for)."""
+    out = _D()
+    _check(load_library().ppl_sigma_for(a, b, R, omega, G, T, ctypes.byref(out)), "ppl_sigma_for")
+    return out.value
+
+
+def gamma_planar(a, b, R, omega, G, T, sigma, kappa) -> float:
+    """Planar surface tension (ppl_gamma_planar)."""
+    out = _D()
+    _check(load_library().ppl_gamma_planar(a, b, R, omega, G, T, sigma, kappa, ctypes.byref(out)),
+           "ppl_gamma_planar")
+    return out.value
+
+
+def kappa_for(a_base, n_base, n, b, R, omega, G, T_ratio, kappa_base=0.0) -> float:
+    """Kappa of a refined mesh (ppl_kappa_for)."""
+    out = _D()
+    _check(load_library().ppl_kappa_for(a_base, n_base, n, b, R, omega, G, T_ratio, kappa_base, ctypes.byref(out)),
+           "ppl_kappa_for")
+    return out.value
+
+
+def refine(cfg: dict, n_base: int, n: int, T_ratio: float) -> dict:
+    """The Sec. 3 refinement of a configuration dict (ppl_refine); per-node arrays must be absent."""
+    C, keep = make_config(cfg)
+    O = PplConfig()
+    _check(load_library().ppl_refine(ctypes.byref(C), n_base, n, T_ratio, ctypes.byref(O)), "ppl_refine")
+    out = dict(cfg)
+    out.update(nx=O.nx, ny=O.ny, a=O.a, sigma=O.sigma, kappa=O.kappa, gx=O.gx, gy=O.gy, T_ref=O.T_ref,
+               T_side=[O.T_side[i] for i in range(4)])
+    return out
 
 
 def _ptr(a):

@@ -79,3 +79,43 @@ def test_config_validation_rejects_bad_boundaries(lib):
         h = ctypes.c_void_p()
         p = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         assert lib.ppl_init(ctypes.byref(C), p, p, p, p, ctypes.byref(h)) == ppl.PPL_E_INVAL, kw
+
+
+def test_refinement_tools_match_oracle():
+    # product-side sigma / gamma / kappa (Sec. 3.2) against the oracle's quadratures
+    from oracle import thermo
+    from paper_2201_04560_gb300 import ppl
+    e = thermo.PR()
+    for L in (128, 192, 288):
+        a = thermo.refine_a(3 / 49, 128, L)
+        el = thermo.PR(a=a)
+        T = 0.86 * el.Tc
+        assert ppl.sigma_for(a, el.b, el.R, el.omega, el.G, T) == pytest.approx(thermo.sigma_for(el, T), rel=1e-10)
+    T = 0.8 * e.Tc
+    for sig, kap in ((0.1, 0.0), (0.1032, 0.3)):
+        g = ppl.gamma_planar(e.a, e.b, e.R, e.omega, e.G, T, sig, kap)
+        assert g == pytest.approx(thermo.planar_gamma(e, T, sig, kap), rel=1e-7)
+    e0 = thermo.PR()
+    s0 = thermo.sigma_for(e0, 0.86 * e0.Tc)
+    e1 = thermo.PR(a=thermo.refine_a(3 / 49, 128, 192))
+    s1 = thermo.sigma_for(e1, 0.86 * e1.Tc)
+    k = thermo.kappa_for(e0, e1, 0.86, 128, 192, s0, s1)
+    assert ppl.kappa_for(3 / 49, 128, 192, e.b, e.R, e.omega, e.G, 0.86) == pytest.approx(k, abs=1e-7)
+
+
+def test_refine_applies_table1_scaling():
+    # Table 1 / Eq. (a-deltax): a ~ dx^2, T ~ dx^2 (with T_c), g ~ dx^3, grid ~ 1/dx
+    import workloads as W
+    from paper_2201_04560_gb300 import ppl
+    Tc = ppl.tc(3 / 49, 2 / 21, 1.0)
+    base = W.base_config(128, 64, gy=-2.5e-5, sigma=0.103, T_side=[0.9 * Tc] * 4, T_ref=0.86 * Tc,
+                         hydro_bc=[W.PERIODIC, W.PERIODIC, W.WALL, W.WALL],
+                         thermal_bc=[W.T_PERIODIC, W.T_PERIODIC, W.T_DIRICHLET, W.T_DIRICHLET])
+    out = ppl.refine(base, 128, 192, 0.86)
+    r = 192 / 128
+    assert (out["nx"], out["ny"]) == (192, 96)
+    assert out["a"] == pytest.approx(3 / 49 / r ** 2, rel=1e-14)
+    assert out["gy"] == pytest.approx(-2.5e-5 / r ** 3, rel=1e-14)
+    assert out["T_side"][2] == pytest.approx(0.9 * Tc / r ** 2, rel=1e-12)
+    assert out["sigma"] == pytest.approx(0.115, abs=5e-4)     # Table 2, L = 192
+    assert 1 - out["kappa"] == pytest.approx(1 + 5.17e-2, rel=1e-2)  # Sec. 3.2
