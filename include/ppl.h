@@ -124,6 +124,7 @@ typedef struct ppl_norms_t {
 } ppl_norms_t;
 
 typedef struct ppl_sim ppl_t;
+typedef struct ppl_batch ppl_batch_t; /* a set of handles stepped together (ppl_batch_create) */
 
 /* Allocate device state and initialise it: f = f^eq(rho0, u0) (Eq. EquilibriumDistribution),
  * T = T0; Dirichlet nodes take their wall value and an outflow line copies the first
@@ -255,6 +256,57 @@ int ppl_kappa_for(double a_base, int32_t n_base, int32_t n, double b, double R, 
  * (n / n_base)^2 refined steps. Per-boundary-node arrays must be rebuilt by the caller
  * (PPL_E_INVAL if base has any). */
 int ppl_refine(const ppl_config *base, int32_t n_base, int32_t n, double T_ratio, ppl_config *out);
+
+/* ---- mesh refinement sequence (Sec. 3, Sec. 4.1-4.3) ---- */
+
+/* Cross-grid difference of Eqs. (rel-diff-timestep) and (global-rel-diff): the field of
+ * `coarse` is interpolated bilinearly onto every node of `fine` and
+ *   *num = sum_fine |I(coarse) - fine|,   *den = sum_fine |fine|        (FP64 sums),
+ * so num/den is the relative L1 difference of the two meshes and sum over several output
+ * times of num / sum of den is the global one. field: 0 = rho, 1 = T. The two handles
+ * cover the same physical domain with the same hydrodynamic sides (PPL_E_INVAL
+ * otherwise); their sizes are arbitrary. Coordinates map cell-centred on periodic axes
+ * (fine line g sits at coarse (g + 1/2) nc/nf - 1/2, wrapping) and node-aligned on bounded
+ * axes (g (nc - 1)/(nf - 1), end lines on end lines). Outflow lines read their copied
+ * first interior line, as everywhere in this library. Reads the current state of both
+ * handles (after all work queued on both streams); synchronises; temporary device memory
+ * is allocated and freed inside the call. */
+int ppl_cross_norm(const ppl_t *coarse, const ppl_t *fine, int field, double *num, double *den);
+
+/* A batch of n (1..64) distinct handles advanced together: one outer step advances
+ * handle k by substeps[k] >= 1 steps (with dt ~ dx^2 a refinement sequence dx, dx/2, dx/4
+ * takes 1, 4, 16). The handles' grids run concurrently, as the branches of one CUDA graph
+ * per outer step (two outer steps when a substep count is odd, so that every ping-pong
+ * buffer returns to its slot); the graph is captured on first use and re-captured only
+ * when the isothermal/energy pattern changes (cfg.iso_steps) or a handle's launch shape
+ * changed (ppl_set_launch, ppl_autotune). Results are identical, bit for bit, to calling
+ * ppl_step(h_k, outer * substeps[k]) on each handle. The handles stay owned by the caller
+ * and must outlive the batch; the batch owns its own streams. */
+int ppl_batch_create(ppl_t *const *sims, const int32_t *substeps, int32_t n, ppl_batch_t **out);
+/* Advance every handle of the batch by `outer` outer steps; the work is ordered after
+ * everything already queued on the handles' streams, and those streams continue after it.
+ * Synchronises and returns the first non-OK status of the handles (PPL_E_NUMERIC). */
+int ppl_batch_step(ppl_batch_t *b, int64_t outer);
+void ppl_batch_destroy(ppl_batch_t *b);
+
+/* ---- launch shape ---- */
+
+/* Rows per CTA of the fused step kernel (the grid is ceil(nx / (NT - 6)) strips of
+ * columns x ceil(ny / rows) row blocks; every CTA recomputes 6 halo rows). rows = 0
+ * restores the default: one wave of resident CTAs over the rows, at least 8 rows each.
+ * 1 <= rows <= ny otherwise (PPL_E_INVAL). Results do not depend on the shape except
+ * through the rounding of the domain-mass sum of Eq. (gravitational_force), which is
+ * summed per CTA (last-bit differences of rho_bar where gravity is on). Drops the
+ * handle's captured graphs; synchronises. */
+int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
+int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
+
+/* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 4..256) with
+ * CUDA events on the handle's stream, keeps the fastest, and restores the state, step
+ * counter and launch count it found (the state is copied aside into temporary device
+ * memory). *best_rows / *best_ms (may be NULL) receive the choice and its time per step.
+ * PPL_E_NUMERIC if the handle's status already reports a numerical failure. */
+int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms);
 
 #ifdef __cplusplus
 }

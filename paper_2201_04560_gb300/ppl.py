@@ -108,9 +108,19 @@ def load_library(build_if_missing: bool = True):
         getattr(L, name).restype = ctypes.c_int
     L.ppl_refine_a.argtypes = [_D, ctypes.c_int32, ctypes.c_int32]
     L.ppl_refine_a.restype = _D
+    L.ppl_cross_norm.argtypes = [H, H, ctypes.c_int, _PD, _PD]
+    L.ppl_batch_create.argtypes = [ctypes.POINTER(H), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                   ctypes.POINTER(H)]
+    L.ppl_batch_step.argtypes = [H, ctypes.c_int64]
+    L.ppl_batch_destroy.argtypes = [H]
+    L.ppl_batch_destroy.restype = None
+    L.ppl_set_launch.argtypes = [H, ctypes.c_int32]
+    L.ppl_get_launch.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.ppl_autotune.argtypes = [H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _PD]
     for name in ("ppl_init", "ppl_reset", "ppl_set_stream", "ppl_step", "ppl_step_async", "ppl_sync",
                  "ppl_fields", "ppl_fields_device", "ppl_populations", "ppl_norms", "ppl_save", "ppl_load",
-                 "ppl_maxwell"):
+                 "ppl_maxwell", "ppl_cross_norm", "ppl_batch_create", "ppl_batch_step", "ppl_set_launch",
+                 "ppl_get_launch", "ppl_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -288,10 +298,71 @@ class Simulation:
     def launch_count(self) -> int:
         return int(self.lib.ppl_launch_count(self.h))
 
+    def set_launch(self, rows_per_cta: int = 0):
+        """Rows per CTA of the step kernel (0 = default shape)."""
+        _check(self.lib.ppl_set_launch(self.h, int(rows_per_cta)), "ppl_set_launch")
+
+    def launch(self):
+        """(rows per CTA, CTAs per step launch)."""
+        r, c = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.ppl_get_launch(self.h, ctypes.byref(r), ctypes.byref(c)), "ppl_get_launch")
+        return r.value, c.value
+
+    def autotune(self, steps: int = 64):
+        """Time the candidate launch shapes, keep the fastest; returns (rows, ms per step)."""
+        r, ms = ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib.ppl_autotune(self.h, int(steps), ctypes.byref(r), ctypes.byref(ms)), "ppl_autotune")
+        return r.value, ms.value
+
     def close(self):
         if self.h:
             self.lib.ppl_destroy(self.h)
             self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cross_norm(coarse: Simulation, fine: Simulation, field: str = "rho"):
+    """(num, den) of the cross-grid L1 difference, Eqs. (rel-diff-timestep), (global-rel-diff):
+    the coarse field interpolated bilinearly onto the fine nodes; num/den is the relative one."""
+    code = {"rho": 0, "T": 1}[field]
+    num, den = ctypes.c_double(), ctypes.c_double()
+    _check(coarse.lib.ppl_cross_norm(coarse.h, fine.h, code, ctypes.byref(num), ctypes.byref(den)),
+           "ppl_cross_norm")
+    return num.value, den.value
+
+
+class Batch:
+    """Handles advanced together, handle k by substeps[k] steps per outer step (Sec. 3:
+    dt ~ dx^2), their grids running concurrently as the branches of one CUDA graph."""
+
+    def __init__(self, sims, substeps):
+        if len(sims) != len(substeps):
+            raise ValueError("one substep count per simulation")
+        self.lib = load_library()
+        self.sims = list(sims)  # keeps the handles alive while the batch exists
+        hs = (ctypes.c_void_p * len(sims))(*[s.h.value for s in sims])
+        subs = (ctypes.c_int32 * len(sims))(*[int(k) for k in substeps])
+        self.b = ctypes.c_void_p()
+        _check(self.lib.ppl_batch_create(hs, subs, len(sims), ctypes.byref(self.b)), "ppl_batch_create")
+
+    def step(self, outer: int = 1):
+        _check(self.lib.ppl_batch_step(self.b, int(outer)), "ppl_batch_step")
+
+    def close(self):
+        if self.b:
+            self.lib.ppl_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
 
     def __del__(self):
         try:

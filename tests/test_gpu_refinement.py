@@ -1,0 +1,163 @@
+"""GPU: the mesh-refinement tools of the library through the C ABI — the cross-mesh
+difference (Eqs. rel-diff-timestep, global-rel-diff) against the oracle's on oracle-run
+fields, the batched refinement sequence (Sec. 3: dt ~ dx^2 substeps) against separately
+stepped handles, and the launch-shape setter / autotuner (results unchanged)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import norms, oracle, thermo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04560_gb300 import ppl as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def th():
+    e = thermo.PR()
+    return {"e": e, 0.8: thermo.maxwell(e, 0.8 * e.Tc), 0.86: thermo.maxwell(e, 0.86 * e.Tc)}
+
+
+def droplet(th, n, precision="fp64", **kw):
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    return W.static_droplet(e.Tc, rv, rl, nx=n, ny=n, R0=n / 4.0, width=3.0 * n / 40, precision=precision, **kw)
+
+
+def pool(th, nx, ny):
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    return W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=nx, ny=ny, g=3e-5)
+
+
+@pytest.mark.parametrize("case", ["droplet", "pool"])
+def test_cross_norm_matches_oracle(ppl, th, case):
+    # two meshes of one problem, each advanced on the GPU and in the oracle; the GPU
+    # difference of the GPU fields against the oracle difference of the oracle fields
+    if case == "droplet":
+        (cc, icc), (cf, icf), steps, px, py = droplet(th, 40), droplet(th, 61), (30, 60), True, True
+    else:
+        (cc, icc), (cf, icf), steps, px, py = pool(th, 48, 40), pool(th, 73, 61), (40, 90), True, False
+    sc, sf = ppl.Simulation(cc, *icc), ppl.Simulation(cf, *icf)
+    sc.step(steps[0])
+    sf.step(steps[1])
+    oc, of = oracle.Oracle(cc, *icc), oracle.Oracle(cf, *icf)
+    oc.step(steps[0])
+    of.step(steps[1])
+    foc, fof = oc.fields(), of.fields()
+    for field in ("rho", "T"):
+        num, den = ppl.cross_norm(sc, sf, field)
+        wnum, wden = norms.rel_diff_terms(foc[field], fof[field], px, py)
+        # the two states agree to the FP64 parity bound (1e-10 relative)
+        assert den == pytest.approx(wden, rel=1e-10)
+        assert num == pytest.approx(wnum, rel=1e-8, abs=1e-10 * wden)
+    # same handle against itself: zero difference
+    num, den = ppl.cross_norm(sf, sf, "rho")
+    assert num < 1e-14 * den
+    sc.close()
+    sf.close()
+
+
+def test_cross_norm_rejects_different_boundaries(ppl, th):
+    (c1, i1), (c2, i2) = droplet(th, 40), pool(th, 48, 40)
+    a, b = ppl.Simulation(c1, *i1), ppl.Simulation(c2, *i2)
+    with pytest.raises(ppl.PplError):
+        ppl.cross_norm(a, b, "rho")
+    a.close()
+    b.close()
+
+
+def _sequence(ppl, th, precision):
+    base, ic = droplet(th, 24, precision=precision, kappa=0.2)
+    base.update(gy=-2e-5, energy_on=1, iso_steps=5, cv=6.0, lambda_l=0.2, lambda_v=0.2)
+    cfgs, ics = [], []
+    for n in (24, 48, 96):
+        c = ppl.refine(base, 24, n, 0.8)
+        c.update(precision=precision)
+        cfgs.append(c)
+        _, icn = droplet(th, n, precision=precision)
+        rho, ux, uy, _ = icn
+        ics.append((rho, ux, uy, np.full_like(rho, c["T_ref"])))
+    return cfgs, ics
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("subs,outer", [((1, 4, 16), 3), ((1, 2, 3), 7)])
+def test_batch_equals_separate_handles(ppl, th, precision, subs, outer):
+    cfgs, ics = _sequence(ppl, th, precision)
+    batch_sims = [ppl.Simulation(c, *ic) for c, ic in zip(cfgs, ics)]
+    with ppl.Batch(batch_sims, subs) as b:
+        b.step(outer)
+        b.step(1)
+    for k, (c, ic) in enumerate(zip(cfgs, ics)):
+        ref = ppl.Simulation(c, *ic)
+        ref.step((outer + 1) * subs[k])
+        np.testing.assert_array_equal(batch_sims[k].populations(), ref.populations())
+        np.testing.assert_array_equal(batch_sims[k].fields()["T"], ref.fields()["T"])
+        assert batch_sims[k].launch_count == ref.launch_count == (outer + 1) * subs[k]
+        ref.close()
+        # the handle keeps stepping on its own after the batch
+        batch_sims[k].step(3)
+        batch_sims[k].close()
+
+
+def test_batch_rejects_bad_arguments(ppl, th):
+    c, ic = droplet(th, 24)
+    s = ppl.Simulation(c, *ic)
+    with pytest.raises(ppl.PplError):
+        ppl.Batch([s, s], [1, 4])  # the same handle twice
+    with pytest.raises(ppl.PplError):
+        ppl.Batch([s], [0])
+    s.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_launch_shape_does_not_change_results(ppl, th, precision, rtol):
+    # gravity off: the domain-mass sum (the only shape-dependent rounding) does not enter;
+    # interior and boundary row blocks are separate compiled specialisations, so only
+    # contraction-level rounding may differ
+    c, ic = droplet(th, 70, precision=precision, kappa=0.3)
+    c["nx"] = c["ny"] = 70
+    ref = ppl.Simulation(c, *ic)
+    ref.step(40)
+    want = ref.populations()
+    ref.close()
+    for rows in (1, 3, 8, 13, 70):
+        s = ppl.Simulation(c, *ic)
+        s.set_launch(rows)
+        assert s.launch()[0] == rows
+        s.step(40)
+        np.testing.assert_allclose(s.populations(), want, rtol=rtol, atol=rtol * 1e-2)
+        s.close()
+
+
+def test_autotune_restores_state(ppl, th):
+    c, ic = pool(th, 300, 160)
+    c.update(gy=-3e-5)
+    s = ppl.Simulation(c, *ic)
+    s.step(10)
+    f0, n0 = s.populations(), s.launch_count
+    rows, ms = s.autotune(8)
+    assert rows >= 1 and ms > 0
+    assert s.launch()[0] == rows
+    np.testing.assert_array_equal(s.populations(), f0)
+    assert s.launch_count == n0
+    s.step(50)
+    got = s.fields()
+    s.set_launch(0)
+    s.close()
+    ref = ppl.Simulation(c, *ic)
+    ref.step(60)
+    want = ref.fields()
+    ref.close()
+    # gravity on: the per-CTA mass partials round differently, nothing else differs
+    for k in ("rho", "T"):
+        np.testing.assert_allclose(got[k], want[k], rtol=1e-12)
