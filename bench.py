@@ -173,6 +173,57 @@ def run_reference(args):
     }))
 
 
+def _json_ready(x):
+    if isinstance(x, dict):
+        return {str(k): _json_ready(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_json_ready(v) for v in x]
+    if hasattr(x, "item"):
+        return x.item()
+    return x
+
+
+# The paper's mesh-refinement studies (Secs. 4.1, 4.3): name -> (study, keyword arguments)
+EXPERIMENTS = {
+    # droplet vaporization, 128^2 / 256^2 / 512^2 with 1:4:16 steps, R = 40 on 256^2, 0.8 / 0.9 T_c,
+    # kappa 0.3, lambda 0.25; D^2-law slope per mesh
+    "droplet-refinement": ("droplet_vaporization_study", dict(meshes=(128, 256, 512), R0=20.0, coarse_steps=200000,
+                                                               sample_every=500)),
+    # Table 2: L = 128 ... 432 (ratio 1.5), T_sat 0.86 T_c, vapour at T_c, lambda 2/3, 0.4e6 steps
+    "table2": ("droplet_vaporization_study", dict(meshes=(128, 192, 288, 432), R0=32.0, T_ratio=0.86,
+                                                  Tv_ratio=1.0, lam=2.0 / 3.0, kappa=0.0, width=2.0 / 0.92,
+                                                  coarse_steps=400000, sample_every=64)),
+    # contact-angle table: psi-based model, rho_w = 4.0 / 2.3 / 1.7, meshes 160 ... 810
+    "contact-psi": ("contact_angle_study", dict(meshes=(160, 240, 360, 540, 810))),
+    # G_w table: modified psi-based model, G_w per mesh keeping the angle of G_w = -0.8 on 160^2
+    "gw-search": ("G_w_search", dict()),
+    # pool boiling, rho_wh = 3.44 and T_h = 1.2 T_c: d^N, D^N, Q(t), time shifts
+    "pool-refinement": ("pool_boiling_study", dict()),
+    # sigma and kappa of the 192^2 mesh tuned on the lattice with sensitivity runs (Sec. 3.2)
+    "calibration": ("calibration.calibrate_mesh", dict(n_base=128, n=192)),
+}
+
+
+def run_experiment(args):
+    import importlib
+    name = args.experiment
+    fn, kw = EXPERIMENTS[name]
+    mod, _, fname = fn.rpartition(".")
+    study = getattr(importlib.import_module("paper_2201_04560_gb300." + (mod or "refinement")), fname)
+    kw = dict(kw)
+    if args.coarse_steps:
+        kw["coarse_steps"] = args.coarse_steps
+    if args.precision in ("fp32", "fp64") and not mod and fname != "G_w_search":
+        kw["precision"] = args.precision
+    t0 = time.time()
+    if name == "contact-psi":
+        out = {"runs": [study(value=v, **kw) for v in (4.0, 2.3, 1.7)]}
+    else:
+        out = study(**kw)
+    out = {"experiment": name, "wall_seconds": time.time() - t0, **out}
+    print(json.dumps(_json_ready(out)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,9 +236,14 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
     ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling runs; the bench workload is 2048)")
     ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling runs; the bench workload is 4096)")
+    ap.add_argument("--experiment", default=None, choices=sorted(EXPERIMENTS),
+                    help="run one of the paper's mesh-refinement studies instead of the throughput step")
+    ap.add_argument("--coarse-steps", type=int, default=0, help="experiment length in first-mesh steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.experiment:
+        return run_experiment(args)
     if args.impl == "reference":
         return run_reference(args)
 

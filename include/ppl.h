@@ -51,6 +51,13 @@ extern "C" {
 /* ---- enumerations ---- */
 #define PPL_FP64 0    /* populations and arithmetic in FP64 */
 #define PPL_FP32DEV 1 /* FP32 arithmetic; f_i - w_i rho_ref and T - T_ref stored in FP32 */
+/* FP64 state that also carries its derivative with respect to sigma (Eq. S) or kappa
+ * (Eq. Q): forward-mode (tangent-linear) sensitivity, read with ppl_tangent_fields. The
+ * initial state has zero derivative. rho_bar of Eq. (gravitational_force) is taken as
+ * parameter-independent (its derivative is zero whenever mass is conserved). Not accepted by
+ * ppl_step_noalloc, ppl_cross_norm or ppl_wall_heat_flux; ppl_phase_area reads the values. */
+#define PPL_FP64_DSIGMA 2
+#define PPL_FP64_DKAPPA 3
 
 #define PPL_PERIODIC 0 /* hydrodynamic side kinds */
 #define PPL_WALL 1     /* Zou-He no-slip wet node + psi-based adhesion (Sec. 2.2) */
@@ -60,7 +67,8 @@ extern "C" {
 #define PPL_T_DIRICHLET 1 /* boundary nodes held at T_side / T_w */
 #define PPL_T_ADIABATIC 2 /* mirror ghost across the wall row (zero normal gradient) */
 
-#define PPL_CONTACT_PSI 0 /* psi-based contact angle model (Eq. psi-based-formula) */
+#define PPL_CONTACT_PSI 0     /* psi-based contact angle model (Eq. psi-based-formula) */
+#define PPL_CONTACT_MOD_PSI 1 /* modified psi-based model (Eq. mod-psi-based-formula), constant G_w */
 
 /* status-word bits (ppl_norms.flags) */
 #define PPL_FLAG_PSI_NEG 1u /* 2 (p_EOS - rho/3) / G < 0 somewhere: psi undefined */
@@ -89,7 +97,10 @@ extern "C" {
  *                sides 0/1, nx for sides 2/3; NULL = use the per-side value). T_dirichlet
  *                marks each node Dirichlet (1) or adiabatic (0) on a wall side. At corners
  *                the y-sides decide the thermal kind and value.
- *  contact_model PPL_CONTACT_PSI (the only model of the hot path); G_w reserved
+ *  contact_model PPL_CONTACT_PSI: solid links carry psi(rho_w, T) in F^m and Q (Eqs.
+ *                psi-based-formula, Q-psi-based). PPL_CONTACT_MOD_PSI: F^ads = -G_w psi^2
+ *                sum_solid w_i c_i and Q drops the solid links (Eqs. mod-psi-based-formula,
+ *                Q-mod-psi-based); rho_w is then unused. G_w: finite, used by MOD_PSI only.
  */
 typedef struct ppl_config {
   int32_t nx, ny;
@@ -166,6 +177,11 @@ int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtyp
  * FP64 [9][ny][nx], decoded from the FP32 deviation storage when precision is FP32DEV. */
 int ppl_populations(ppl_t *h, double *f);
 
+/* Derivatives d rho, d u_x, d u_y, d T of the current state with respect to the parameter
+ * of a PPL_FP64_DSIGMA / PPL_FP64_DKAPPA handle, as host FP64 [ny][nx] arrays (NULL
+ * pointers skip a field). PPL_E_INVAL for other handles. Synchronises. */
+int ppl_tangent_fields(ppl_t *h, double *drho, double *dux, double *duy, double *dT);
+
 /* FP64 diagnostics of the current state; synchronises. */
 int ppl_norms(ppl_t *h, ppl_norms_t *out);
 
@@ -229,6 +245,10 @@ double ppl_tc(double a, double b, double R);
 int ppl_maxwell(double a, double b, double R, double omega, double T, double *rho_v,
                 double *rho_l, double *p_sat);
 
+/* Peng-Robinson pressure of Eq. (peng-robinson) at (rho, T) and its derivative dp/drho at
+ * fixed T (any T > 0, including supercritical). PPL_E_INVAL outside b rho < 1. Host only. */
+int ppl_pressure(double a, double b, double R, double omega, double T, double rho, double *p, double *dp_drho);
+
 /* Eq. (a-deltax): a on a mesh of n nodes per length, from a_base on n_base nodes. */
 double ppl_refine_a(double a_base, int32_t n_base, int32_t n);
 
@@ -253,7 +273,7 @@ int ppl_kappa_for(double a_base, int32_t n_base, int32_t n, double b, double R, 
  * Eq. (a-deltax); temperatures (T_side, T_ref) with T_c (~ dx^2); gravity ~ dx^3 (Table 1);
  * sigma tuned at T_ratio T_c; kappa per Eq. (gamma-meshes-relation). lambda, c_v, eta, rho_w
  * and the MRT rates are O(1) and kept. The time step scales as dx^2: one base step is
- * (n / n_base)^2 refined steps. Per-boundary-node arrays must be rebuilt by the caller
+ * (n / n_base)^2 refined steps, and iso_steps is scaled by that factor. Per-boundary-node arrays must be rebuilt by the caller
  * (PPL_E_INVAL if base has any). */
 int ppl_refine(const ppl_config *base, int32_t n_base, int32_t n, double T_ratio, ppl_config *out);
 
@@ -263,7 +283,8 @@ int ppl_refine(const ppl_config *base, int32_t n_base, int32_t n, double T_ratio
  * `coarse` is interpolated bilinearly onto every node of `fine` and
  *   *num = sum_fine |I(coarse) - fine|,   *den = sum_fine |fine|        (FP64 sums),
  * so num/den is the relative L1 difference of the two meshes and sum over several output
- * times of num / sum of den is the global one. field: 0 = rho, 1 = T. The two handles
+ * times of num / sum of den is the global one. field: 0 = rho, 1 = the reduced temperature
+ * T / T_c of each mesh (T_c ~ a scales with dx^2 under Table 1's refinement). The two handles
  * cover the same physical domain with the same hydrodynamic sides (PPL_E_INVAL
  * otherwise); their sizes are arbitrary. Coordinates map cell-centred on periodic axes
  * (fine line g sits at coarse (g + 1/2) nc/nf - 1/2, wrapping) and node-aligned on bounded
@@ -289,6 +310,49 @@ int ppl_batch_create(ppl_t *const *sims, const int32_t *substeps, int32_t n, ppl
 int ppl_batch_step(ppl_batch_t *b, int64_t outer);
 void ppl_batch_destroy(ppl_batch_t *b);
 
+/* Liquid area of the current state for the droplet radius R(t) of Sec. 4.1:
+ *   *area = sum over the nodes of clamp((rho - rho_lo) / (rho_hi - rho_lo), 0, 1)   (FP64),
+ * a volume-fraction count in lattice nodes (R = sqrt(area / pi) for one droplet). Outflow
+ * lines count their copied first interior line. rho_hi > rho_lo (PPL_E_INVAL otherwise);
+ * runs after all work queued on the handle's stream and synchronises it. */
+int ppl_phase_area(ppl_t *h, double rho_lo, double rho_hi, double *area);
+
+/* Eq. (relative-change-R): *out = sum_i |R[i] - R_star[i]| / sum_i |R_star[i]| over n >= 1
+ * samples of two series taken at the same physical times (R_star on the finer mesh, both in
+ * the same length unit). Host only. PPL_E_INVAL for n < 1 or an all-zero R_star. */
+int ppl_relative_change(const double *R, const double *R_star, int64_t n, double *out);
+
+/* Eq. (pool-heat-flux): mean conductive heat flux entering the domain through boundary
+ * line `side` (0 = x-min, 1 = x-max, 2 = y-min, 3 = y-max),
+ *   *q = (1/L) sum over the L nodes of the line of -lambda(rho) dT/dn,
+ * n the inward normal, dT/dn = (-3 T_0 + 4 T_1 - T_2) / 2 from the line and the next two
+ * lines inward (second-order one-sided), lambda(rho) linear between (rho_v, lambda_v) and
+ * (rho_l, lambda_l) as in the energy equation. Positive when heat enters the fluid.
+ * PPL_E_INVAL for a side with neither a hydrodynamic nor a thermal boundary, or fewer than
+ * 3 lines across. Synchronises the handle's stream. */
+int ppl_wall_heat_flux(ppl_t *h, int side, double *q);
+
+/* Time shift of Eq. (rel-diff-minimize): with `coarse` at time tau - m (its own steps) and
+ * `finest` at tau, evaluates sum_fine |I(theta^coarse) - theta^finest| (the numerator of
+ * ppl_cross_norm) at the shifts delta = -m, -m + stride, ..., <= m, stepping `coarse` by
+ * `stride` between evaluations, and returns the minimising shift in *delta (coarse steps)
+ * and the minimum in *num_min (may be NULL). `coarse` is left at the last shift evaluated.
+ * field: 0 = rho, 1 = T. m >= 0, stride >= 1; same hydrodynamic sides (PPL_E_INVAL).
+ * Synchronises both handles' streams. */
+int ppl_time_shift(ppl_t *coarse, const ppl_t *finest, int field, int64_t m, int64_t stride, int64_t *delta,
+                   double *num_min);
+
+/* Contact angle (degrees, measured through the liquid) of one droplet on boundary line
+ * `side` of a host density field rho[ny][nx] (e.g. from ppl_fields), read as a circular cap
+ * (Sec. 4.3.1 contact-angle tests). The base is the first line from the wall inward (within
+ * half the domain) whose densest node exceeds rho_mid with a crossing of rho = rho_mid on
+ * each side; from its half-width a, its distance n0 from the wall and the crossing h along
+ * the inward line through the base centre, the circle through (+-a, n0) and (0, h) gives
+ * theta = 90 deg + asin(yc / Rc), clamped to [0, 180] (yc: height of its centre above the
+ * wall line; a droplet that left the wall reads 180). Crossings by linear interpolation.
+ * Host only. PPL_E_INVAL when no base or top is found (e.g. a film over the whole wall). */
+int ppl_contact_angle(const double *rho, int32_t nx, int32_t ny, int side, double rho_mid, double *theta);
+
 /* ---- launch shape ---- */
 
 /* Rows per CTA of the fused step kernel (the grid is ceil(nx / (NT - 6)) strips of
@@ -301,7 +365,7 @@ void ppl_batch_destroy(ppl_batch_t *b);
 int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
 
-/* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 4..256) with
+/* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256) with
  * CUDA events on the handle's stream, keeps the fastest, and restores the state, step
  * counter and launch count it found (the state is copied aside into temporary device
  * memory). *best_rows / *best_ms (may be NULL) receive the choice and its time per step.

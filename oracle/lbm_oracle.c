@@ -84,6 +84,9 @@ typedef struct {
   const uint8_t *T_dirichlet[4]; /* optional per-boundary-node kind: 1 Dirichlet, 0 adiabatic */
   double rho_bar_fixed; /* finite: the domain-mean density of Eq. (gravitational_force) is given
                            (the grid is a window of a larger domain); NaN: mean over this grid */
+  int32_t contact_model; /* 0: psi-based (Eq. psi-based-formula); 1: modified psi-based
+                            (Eq. mod-psi-based-formula) with the constant G_w below */
+  double G_w;
 } orc_params;
 
 /* M^-1 = M^T diag(1/|row_k|^2): rows of M are orthogonal */
@@ -347,16 +350,27 @@ static long macro(const orc_params *P, const double *f, const double *T, work_t 
     for (int x = 0; x < P->nx; ++x) {
       size_t k = IDX(x, y);
       double sx = 0.0, sy = 0.0;
+      double ax = 0.0, ay = 0.0; /* sum of w_i s(x + c_i) c_i over the solid links */
       for (int i = 1; i < 9; ++i) {
         int ox, oy, side;
         double pn;
-        if (neighbour(P, x, y, CX[i], CY[i], &ox, &oy, &side) == 0) pn = w->psi[IDX(ox, oy)];
-        else if (pr_psi(P, wall_rho_w(P, side, x, y), T[k], &pn)) return 2 + (long)k;
+        if (neighbour(P, x, y, CX[i], CY[i], &ox, &oy, &side) == 0) {
+          pn = w->psi[IDX(ox, oy)];
+        } else if (P->contact_model == 1) {
+          ax += WF[i] * CX[i];
+          ay += WF[i] * CY[i];
+          continue;
+        } else if (pr_psi(P, wall_rho_w(P, side, x, y), T[k], &pn)) {
+          return 2 + (long)k;
+        }
         sx += WF[i] * pn * CX[i];
         sy += WF[i] * pn * CY[i];
       }
-      w->Fmx[k] = -P->G * w->psi[k] * sx;
-      w->Fmy[k] = -P->G * w->psi[k] * sy;
+      /* Eq. (shanchen-walls): fluid links plus F^ads; the modified model's F^ads is
+         -G_w psi^2 sum_solid w_i c_i (Eq. mod-psi-based-formula) */
+      const double ps = w->psi[k];
+      w->Fmx[k] = -P->G * ps * sx - P->G_w * ps * ps * ax;
+      w->Fmy[k] = -P->G * ps * sy - P->G_w * ps * ps * ay;
       w->Fx[k] = w->Fmx[k] + P->gx * (w->rho[k] - *rho_bar);
       w->Fy[k] = w->Fmy[k] + P->gy * (w->rho[k] - *rho_bar);
     }
@@ -449,12 +463,14 @@ long orc_step(const orc_params *P, double *f, double *T, int64_t step) {
       S[6] = -Fy;
       S[7] = 2.0 * (ux * Fx - uy * Fy);
       S[8] = ux * Fy + uy * Fx;
-      /* Eqs. (Q), (Q-psi-based): solid links use psi(rho_w(x), T(x)) */
+      /* Eqs. (Q), (Q-psi-based): solid links use psi(rho_w(x), T(x)); Eq. (Q-mod-psi-based):
+         the modified model drops them (psi(x + c_i) replaced by psi(x)) */
       double Qxx = 0.0, Qyy = 0.0, Qxy = 0.0;
       for (int i = 1; i < 9; ++i) {
         int ox, oy, side;
         double pn;
         if (neighbour(P, x, y, CX[i], CY[i], &ox, &oy, &side) == 0) pn = w.psi[IDX(ox, oy)];
+        else if (P->contact_model == 1) pn = psi;
         else pr_psi(P, wall_rho_w(P, side, x, y), T[k], &pn);
         double d = WF[i] * (pn - psi);
         Qxx += d * CX[i] * CX[i];

@@ -36,6 +36,7 @@ class OrcParams(ctypes.Structure):
         ("T_side", _D * 4), ("rho_w_side", _D * 4),
         ("rho_w", _PD * 4), ("T_w", _PD * 4), ("T_dirichlet", _PU8 * 4),
         ("rho_bar_fixed", _D),
+        ("contact_model", ctypes.c_int32), ("G_w", _D),
     ]
 
 
@@ -89,6 +90,8 @@ def make_params(cfg: dict):
     for i in range(9):
         P.s[i] = float(cfg["s"][i])
     P.rho_bar_fixed = float(cfg.get("rho_bar_fixed", float("nan")))
+    P.contact_model = int(cfg.get("contact_model", 0))
+    P.G_w = float(cfg.get("G_w", 0.0))
     P.energy_on = int(cfg["energy_on"])
     P.iso_steps = int(cfg["iso_steps"])
     for sd in range(4):

@@ -17,9 +17,10 @@ UNITS = {
     "thermo.cu": [],
     "step_fp64.cu": [],
     "step_fp32.cu": ["--use_fast_math"],
+    "step_tangent.cu": [],
 }
 SOURCES = [os.path.join(CSRC, u) for u in UNITS]
-DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "row_step.cuh", "step_variants.h")] + [
+DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "dual.cuh", "row_step.cuh", "step_variants.h")] + [
     os.path.join(ROOT, "include", "ppl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -13,6 +13,8 @@
 
 #include <cstdint>
 
+#include "dual.cuh"
+
 namespace ppl_dev {
 
 enum { PERIODIC = 0, WALL = 1, OUTFLOW = 2 };
@@ -41,6 +43,8 @@ struct Params {
   real twoG_inv;     // 2 / G
   real cv_inv;       // 1 / c_v
   double inv_nodes;  // 1 / (nx ny)
+  int mod_psi;       // wall adhesion: 0 psi-based, 1 modified psi-based
+  real Gw_over_G;    // G_w / G of the modified model
 };
 
 struct StepIO {
@@ -311,6 +315,11 @@ __device__ __forceinline__ void collide(const Params<real> &P, real fd[9], real 
 template <typename real>
 __device__ __forceinline__ real ld_real(const void *p, long long k) {
   return __ldg(reinterpret_cast<const real *>(p) + k);
+}
+template <>
+__device__ __forceinline__ Dual ld_real<Dual>(const void *p, long long k) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
+  return Dual(v.x, v.y);
 }
 
 

@@ -149,7 +149,11 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
   const real jy = fl[2] - fl[4] + fl[5] + fl[6] - fl[7] - fl[8];
   const real psi_c = sqrt(fmax(psi_arg(P, rho, t), real(0)));
   const int ws = wall_side(P, gx, gy);
-  const real psi_w = ws >= 0 ? sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, gx, gy), t), real(0))) : real(0);
+  // solid links: psi(rho_w, T) (psi-based model) or (G_w / G) psi (modified model, whose
+  // F^ads = -G_w psi^2 sum w c has that form)
+  const real psi_w = ws < 0 ? real(0)
+                     : P.mod_psi ? P.Gw_over_G * psi_c
+                                 : sqrt(fmax(psi_arg(P, wall_rho_w(P, ws, gx, gy), t), real(0)));
   real sx = 0, sy = 0;
   for (int q = 1; q < 9; ++q) {
     const int nxp = gx + kCX[q], nyp = gy + kCY[q];
@@ -171,16 +175,21 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
   const real Fx = -P.G * psi_c * sx + P.gx * (rho - rho_bar);
   const real Fy = -P.G * psi_c * sy + P.gy * (rho - rho_bar);
   const real ux = (jx + real(0.5) * Fx) / rho, uy = (jy + real(0.5) * Fy) / rho;
-  if (dtype == 0) {
+  if (dtype == 2) {  // derivatives of the tangent state (FP64)
+    if (o_rho) ((double *)o_rho)[k] = tangent_of(rho);
+    if (o_ux) ((double *)o_ux)[k] = tangent_of(ux);
+    if (o_uy) ((double *)o_uy)[k] = tangent_of(uy);
+    if (o_T) ((double *)o_T)[k] = tangent_of(t);
+  } else if (dtype == 0) {
     if (o_rho) ((double *)o_rho)[k] = (double)rho;
     if (o_ux) ((double *)o_ux)[k] = (double)ux;
     if (o_uy) ((double *)o_uy)[k] = (double)uy;
     if (o_T) ((double *)o_T)[k] = (double)t;
   } else {
-    if (o_rho) ((float *)o_rho)[k] = (float)rho;
-    if (o_ux) ((float *)o_ux)[k] = (float)ux;
-    if (o_uy) ((float *)o_uy)[k] = (float)uy;
-    if (o_T) ((float *)o_T)[k] = (float)t;
+    if (o_rho) ((float *)o_rho)[k] = (float)value_of(rho);
+    if (o_ux) ((float *)o_ux)[k] = (float)value_of(ux);
+    if (o_uy) ((float *)o_uy)[k] = (float)value_of(uy);
+    if (o_T) ((float *)o_T)[k] = (float)value_of(t);
   }
 }
 
@@ -234,6 +243,7 @@ struct ppl_sim {
   int stats_blocks = 0;
   Params<double> pd;
   Params<float> pf;
+  Params<Dual> pt;  // tangent modes
   uint64_t cfg_hash = 0;
 };
 
@@ -284,16 +294,20 @@ uint64_t hash_config(const ppl_sim *h) {
   return x;
 }
 
+// FP64 state carrying d/d(sigma) or d/d(kappa)
+bool is_tangent(int prec) { return prec == PPL_FP64_DSIGMA || prec == PPL_FP64_DKAPPA; }
+
 int validate(const ppl_config *c) {
   if (!c) return PPL_E_INVAL;
   if (c->nx < 3 || c->ny < 3) return PPL_E_INVAL;
   if ((long long)c->nx * c->ny > (1ll << 34)) return PPL_E_INVAL;
-  if (c->precision != PPL_FP64 && c->precision != PPL_FP32DEV) return PPL_E_INVAL;
+  if (c->precision != PPL_FP64 && c->precision != PPL_FP32DEV && !is_tangent(c->precision)) return PPL_E_INVAL;
   if (!(c->a > 0) || !(c->b > 0) || !(c->R > 0) || !(c->G < 0)) return PPL_E_INVAL;
   for (int i = 0; i < 9; ++i)
     if (!(c->s[i] > 0 && c->s[i] < 2)) return PPL_E_INVAL;
   if (!(c->rho_l != c->rho_v)) return PPL_E_INVAL;
-  if (c->contact_model != PPL_CONTACT_PSI) return PPL_E_INVAL;
+  if (c->contact_model != PPL_CONTACT_PSI && c->contact_model != PPL_CONTACT_MOD_PSI) return PPL_E_INVAL;
+  if (!std::isfinite(c->G_w)) return PPL_E_INVAL;
   if (c->energy_on && !(c->cv > 0)) return PPL_E_INVAL;
   if (c->iso_steps < 0) return PPL_E_INVAL;
   for (int s = 0; s < 4; ++s) {
@@ -353,6 +367,16 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
   P.sigma12_e = (real)(12.0 * c.sigma / (1.0 / c.s[1] - 0.5));
   P.sigma12_z = (real)(12.0 * c.sigma / (1.0 / c.s[2] - 0.5));
   P.kappa_G2 = (real)(c.kappa * c.G / 2.0);
+  if constexpr (is_dual<real>::value) {  // seed the parameter the tangent is taken with
+    if (h->prec == PPL_FP64_DSIGMA) {
+      P.sigma12_e.d = 12.0 / (1.0 / c.s[1] - 0.5);
+      P.sigma12_z.d = 12.0 / (1.0 / c.s[2] - 0.5);
+    } else if (h->prec == PPL_FP64_DKAPPA) {
+      P.kappa_G2.d = c.G / 2.0;
+    }
+  }
+  P.mod_psi = c.contact_model == PPL_CONTACT_MOD_PSI ? 1 : 0;
+  P.Gw_over_G = (real)(c.G_w / c.G);
   P.gx = (real)c.gx;
   P.gy = (real)c.gy;
   P.cv = (real)c.cv;
@@ -379,6 +403,10 @@ template <>
 const Params<double> &params_of<double>(const ppl_sim *h) { return h->pd; }
 template <>
 const Params<float> &params_of<float>(const ppl_sim *h) { return h->pf; }
+template <>
+const Params<Dual> &params_of<Dual>(const ppl_sim *h) { return h->pt; }
+
+
 
 template <typename real>
 int launch_step_t(ppl_sim *h, bool energy) {
@@ -403,7 +431,9 @@ int launch_step_t(ppl_sim *h, bool energy) {
 }
 
 int launch_step(ppl_sim *h, bool energy) {
-  return h->prec == PPL_FP64 ? launch_step_t<double>(h, energy) : launch_step_t<float>(h, energy);
+  return h->prec == PPL_FP64      ? launch_step_t<double>(h, energy)
+         : h->prec == PPL_FP32DEV ? launch_step_t<float>(h, energy)
+                                  : launch_step_t<Dual>(h, energy);
 }
 
 bool energy_at(const ppl_sim *h, int64_t step) { return h->cfg.energy_on && step >= h->cfg.iso_steps; }
@@ -445,7 +475,9 @@ int run_stats(ppl_sim *h, double *stats_dst) {
 }
 
 int stats(ppl_sim *h, double *stats_dst) {
-  return h->prec == PPL_FP64 ? run_stats<double>(h, stats_dst) : run_stats<float>(h, stats_dst);
+  return h->prec == PPL_FP64      ? run_stats<double>(h, stats_dst)
+         : h->prec == PPL_FP32DEV ? run_stats<float>(h, stats_dst)
+                                  : run_stats<Dual>(h, stats_dst);
 }
 
 template <typename real>
@@ -469,8 +501,9 @@ int upload_state(ppl_sim *h, const double *rho0, const double *ux0, const double
   h->cur = 0;
   h->step = 0;
   CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
-  int rc = h->prec == PPL_FP64 ? upload_state_t<double>(h, rho0, ux0, uy0, T0)
-                               : upload_state_t<float>(h, rho0, ux0, uy0, T0);
+  int rc = h->prec == PPL_FP64      ? upload_state_t<double>(h, rho0, ux0, uy0, T0)
+           : h->prec == PPL_FP32DEV ? upload_state_t<float>(h, rho0, ux0, uy0, T0)
+                                    : upload_state_t<Dual>(h, rho0, ux0, uy0, T0);
   if (rc) return rc;
   rc = stats(h, h->stats[0]);
   if (rc) return rc;
@@ -629,7 +662,7 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   h->nx = cfg->nx;
   h->ny = cfg->ny;
   h->N = (long long)cfg->nx * cfg->ny;
-  h->rsz = h->prec == PPL_FP64 ? 8 : 4;
+  h->rsz = h->prec == PPL_FP64 ? 8 : h->prec == PPL_FP32DEV ? 4 : sizeof(Dual);
   for (int s = 0; s < 4; ++s) {
     const int len = s < 2 ? cfg->ny : cfg->nx;
     if (cfg->rho_w[s]) h->h_rho_w[s].assign(cfg->rho_w[s], cfg->rho_w[s] + len);
@@ -649,7 +682,9 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   h->stream = h->own_stream;
 
   // launch shape: strips of (nt - 6) columns, one wave of CTAs over the rows
-  h->var = h->prec == PPL_FP64 ? step_variant_fp64() : step_variant_fp32();
+  h->var = h->prec == PPL_FP64      ? step_variant_fp64()
+           : h->prec == PPL_FP32DEV ? step_variant_fp32()
+                                    : step_variant_tangent();
   for (int e = 0; e < 2; ++e)
     if (cudaFuncSetAttribute(h->var.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->var.smem) !=
         cudaSuccess)
@@ -694,8 +729,12 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
       auto put_real = [&](const std::vector<double> &v, const void **dst) {
         if (v.empty()) return;
         for (size_t i = 0; i < len; ++i) {
-          if (h->rsz == 8) memcpy(&host[off + i * 8], &v[i], 8);
-          else {
+          if (h->rsz == 8) {
+            memcpy(&host[off + i * 8], &v[i], 8);
+          } else if (h->rsz == sizeof(Dual)) {
+            const Dual x(v[i]);
+            memcpy(&host[off + i * sizeof(Dual)], &x, sizeof(Dual));
+          } else {
             const float x = (float)v[i];
             memcpy(&host[off + i * 4], &x, 4);
           }
@@ -715,8 +754,10 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   }
   if (h->prec == PPL_FP64)
     fill_params<double>(h, h->pd, (const double *const *)rw, (const double *const *)tw, td);
-  else
+  else if (h->prec == PPL_FP32DEV)
     fill_params<float>(h, h->pf, (const float *const *)rw, (const float *const *)tw, td);
+  else
+    fill_params<Dual>(h, h->pt, (const Dual *const *)rw, (const Dual *const *)tw, td);
 
   rc = upload_state(h, rho0, ux0, uy0, T0);
   if (rc) return fail(rc);
@@ -770,36 +811,52 @@ int ppl_step(ppl_t *h, int64_t nsteps) {
   return check_status(h);
 }
 
-int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtype) {
-  if (!h || (dtype != 0 && dtype != 1)) return PPL_E_INVAL;
+static int export_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtype) {
   const int nt = 256;
   const unsigned nb = (unsigned)((h->N + nt - 1) / nt);
   if (h->prec == PPL_FP64)
     export_fields<double><<<nb, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur],
                                                     (const double *)h->T[h->cur], h->stats[h->cur], rho, ux, uy,
                                                     T, dtype);
-  else
+  else if (h->prec == PPL_FP32DEV)
     export_fields<float><<<nb, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur],
                                                    (const float *)h->T[h->cur], h->stats[h->cur], rho, ux, uy, T,
                                                    dtype);
+  else
+    export_fields<Dual><<<nb, nt, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], (const Dual *)h->T[h->cur],
+                                                  h->stats[h->cur], rho, ux, uy, T, dtype);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return PPL_OK;
 }
 
-int ppl_fields(ppl_t *h, double *rho, double *ux, double *uy, double *T) {
-  if (!h) return PPL_E_INVAL;
+static int fields_to_host(ppl_t *h, double *rho, double *ux, double *uy, double *T, int dtype) {
   double *d = nullptr;
   const size_t nb = (size_t)h->N * sizeof(double);
   CK(cudaMalloc(&d, 4 * nb));
-  int rc = ppl_fields_device(h, rho ? d : nullptr, ux ? d + h->N : nullptr, uy ? d + 2 * h->N : nullptr,
-                             T ? d + 3 * h->N : nullptr, 0);
+  int rc = export_device(h, rho ? d : nullptr, ux ? d + h->N : nullptr, uy ? d + 2 * h->N : nullptr,
+                         T ? d + 3 * h->N : nullptr, dtype);
   double *dst[4] = {rho, ux, uy, T};
   for (int i = 0; i < 4 && rc == PPL_OK; ++i)
     if (dst[i]) rc = cuda_err(cudaMemcpyAsync(dst[i], d + i * h->N, nb, cudaMemcpyDeviceToHost, h->stream));
   if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
   cudaFree(d);
   return rc;
+}
+
+int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtype) {
+  if (!h || (dtype != 0 && dtype != 1)) return PPL_E_INVAL;
+  return export_device(h, rho, ux, uy, T, dtype);
+}
+
+int ppl_tangent_fields(ppl_t *h, double *drho, double *dux, double *duy, double *dT) {
+  if (!h || !is_tangent(h->prec)) return PPL_E_INVAL;
+  return fields_to_host(h, drho, dux, duy, dT, 2);
+}
+
+int ppl_fields(ppl_t *h, double *rho, double *ux, double *uy, double *T) {
+  if (!h) return PPL_E_INVAL;
+  return fields_to_host(h, rho, ux, uy, T, 0);
 }
 
 int ppl_populations(ppl_t *h, double *f) {
@@ -811,8 +868,10 @@ int ppl_populations(ppl_t *h, double *f) {
   const unsigned blocks = (unsigned)((h->N + nt - 1) / nt);
   if (h->prec == PPL_FP64)
     export_populations<double><<<blocks, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], d);
-  else
+  else if (h->prec == PPL_FP32DEV)
     export_populations<float><<<blocks, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], d);
+  else
+    export_populations<Dual><<<blocks, nt, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], d);
   int rc = cuda_err(cudaGetLastError());
   if (rc == PPL_OK) rc = cuda_err(cudaMemcpyAsync(f, d, nb, cudaMemcpyDeviceToHost, h->stream));
   if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
@@ -947,6 +1006,7 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
                      const double *stats_in, double *stats_out, uint32_t *status, void *cuda_stream) {
   int rc = validate(cfg);
   if (rc) return rc;
+  if (is_tangent(cfg->precision)) return PPL_E_INVAL;  // plain FP64 / FP32 states only
   if (!f_in || !T_in || !f_out || !T_out || !stats_in || !stats_out || !status) return PPL_E_INVAL;
   if (f_in == f_out || T_in == T_out) return PPL_E_INVAL;  // the step reads neighbours of what it writes
   for (int s = 0; s < 4; ++s)
@@ -1030,6 +1090,7 @@ __device__ __forceinline__ double node_value(const Params<real> &P, const real *
   const NodeMap m = map_node(P, x, y);  // outflow lines read their first-interior copy
   const long long k = (long long)m.y * P.nx + m.x;
   if (field == 1) return (double)P.T_ref + (double)T[k];
+  if (field == 2) return ((double)P.T_ref + (double)T[k]) / (double)P.Tc;  // reduced T / T_c
   double d = 0.0;
   for (int q = 0; q < 9; ++q) d += (double)f[q * P.plane + k];
   return (double)P.rho_ref + d;
@@ -1042,6 +1103,7 @@ __global__ void cross_norm_partials(const Params<rc> Pc, const rc *fc, const rc 
   __shared__ double red[2][NT / 32];
   double num = 0.0, den = 0.0;
   const bool perx = Pc.hbc[0] == PERIODIC, pery = Pc.hbc[2] == PERIODIC;
+  const int fv = field == 1 ? 2 : field;  // temperatures compare as T / T_c of each mesh
   for (long long k = (long long)blockIdx.x * NT + threadIdx.x; k < Pf.plane; k += (long long)gridDim.x * NT) {
     const int x = (int)(k % Pf.nx), y = (int)(k / Pf.nx);
     const double X = coarse_coord(x, Pf.nx, Pc.nx, perx), Y = coarse_coord(y, Pf.ny, Pc.ny, pery);
@@ -1062,10 +1124,10 @@ __global__ void cross_norm_partials(const Params<rc> Pc, const rc *fc, const rc 
       y0 = min(max(y0, 0), Pc.ny - 1);
       y1 = min(max(y1, 0), Pc.ny - 1);
     }
-    const double c00 = node_value(Pc, fc, Tc, x0, y0, field), c10 = node_value(Pc, fc, Tc, x1, y0, field);
-    const double c01 = node_value(Pc, fc, Tc, x0, y1, field), c11 = node_value(Pc, fc, Tc, x1, y1, field);
+    const double c00 = node_value(Pc, fc, Tc, x0, y0, fv), c10 = node_value(Pc, fc, Tc, x1, y0, fv);
+    const double c01 = node_value(Pc, fc, Tc, x0, y1, fv), c11 = node_value(Pc, fc, Tc, x1, y1, fv);
     const double I = (1.0 - wy) * ((1.0 - wx) * c00 + wx * c10) + wy * ((1.0 - wx) * c01 + wx * c11);
-    const double v = node_value(Pf, ff, Tf, x, y, field);
+    const double v = node_value(Pf, ff, Tf, x, y, fv);
     num += fabs(I - v);
     den += fabs(v);
   }
@@ -1112,6 +1174,7 @@ extern "C" {
 
 int ppl_cross_norm(const ppl_t *coarse, const ppl_t *fine, int field, double *num, double *den) {
   if (!coarse || !fine || !num || !den || (field != 0 && field != 1)) return PPL_E_INVAL;
+  if (is_tangent(coarse->prec) || is_tangent(fine->prec)) return PPL_E_INVAL;
   for (int s = 0; s < 4; ++s)
     if (coarse->cfg.hydro_bc[s] != fine->cfg.hydro_bc[s]) return PPL_E_INVAL;  // same domain, two meshes
   CK(cudaStreamSynchronize(coarse->stream));
@@ -1423,7 +1486,7 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
   };
 
   std::vector<int> cand = {default_rows(h)};
-  for (int H : {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+  for (int H : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
     if (H <= h->ny && std::find(cand.begin(), cand.end(), H) == cand.end()) cand.push_back(H);
   int best = cand[0];
   float best_t = -1.0f;
@@ -1456,6 +1519,235 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
     if (best_ms) *best_ms = (double)best_t / steps;
   }
   return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Droplet radius of Sec. 4.1: liquid area from the density field, and the relative
+// change of two R(t) series, Eq. (relative-change-R)
+// ---------------------------------------------------------------------------------
+namespace {
+
+template <typename real>
+__global__ void phase_area_partials(const Params<real> P, const real *f, double lo, double inv_span, double *part) {
+  constexpr int NT = 256;
+  __shared__ double red[NT / 32];
+  double acc = 0.0;
+  for (long long k = (long long)blockIdx.x * NT + threadIdx.x; k < P.plane; k += (long long)gridDim.x * NT) {
+    const int x = (int)(k % P.nx), y = (int)(k / P.nx);
+    const double rho = node_value(P, f, f, x, y, 0);
+    acc += fmin(fmax((rho - lo) * inv_span, 0.0), 1.0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_finalize(const double *part, int nblk, double *out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0;
+  for (int i = 0; i < nblk; ++i) a += part[i];
+  out[0] = a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppl_phase_area(ppl_t *h, double rho_lo, double rho_hi, double *area) {
+  if (!h || !area || !(rho_hi > rho_lo)) return PPL_E_INVAL;
+  const int nblk = h->stats_blocks;  // partials holds >= 7 * stats_blocks doubles
+  const double inv = 1.0 / (rho_hi - rho_lo);
+  if (h->prec == PPL_FP64)
+    phase_area_partials<double><<<nblk, 256, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], rho_lo, inv,
+                                                             h->partials);
+  else if (h->prec == PPL_FP32DEV)
+    phase_area_partials<float><<<nblk, 256, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], rho_lo, inv,
+                                                            h->partials);
+  else
+    phase_area_partials<Dual><<<nblk, 256, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], rho_lo, inv,
+                                                           h->partials);
+  CK(cudaGetLastError());
+  sum_finalize<<<1, 32, 0, h->stream>>>(h->partials, nblk, h->norm_out);
+  CK(cudaGetLastError());
+  double out = 0.0;
+  CK(cudaMemcpyAsync(&out, h->norm_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *area = out;
+  return PPL_OK;
+}
+
+int ppl_relative_change(const double *R, const double *R_star, int64_t n, double *out) {
+  if (!R || !R_star || !out || n < 1) return PPL_E_INVAL;
+  double num = 0.0, den = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    num += std::fabs(R[i] - R_star[i]);
+    den += std::fabs(R_star[i]);
+  }
+  if (!(den > 0.0)) return PPL_E_INVAL;
+  *out = num / den;
+  return PPL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Wall heat flux of Eq. (pool-heat-flux): mean over a boundary line of the conductive flux
+// into the domain, lambda(rho) times the inward normal derivative of T, second-order
+// one-sided difference
+// ---------------------------------------------------------------------------------
+namespace {
+
+template <typename real>
+__global__ void wall_flux_partials(const Params<real> P, const real *f, const real *T, int side, double *part) {
+  constexpr int NT = 256;
+  __shared__ double red[NT / 32];
+  const bool xs = side < 2;
+  const int len = xs ? P.ny : P.nx;
+  double acc = 0.0;
+  for (int i = blockIdx.x * NT + threadIdx.x; i < len; i += gridDim.x * NT) {
+    int x[3], y[3];
+    for (int k = 0; k < 3; ++k) {
+      const int d = (side & 1) ? -k : k;  // k nodes inward from the boundary line
+      x[k] = xs ? ((side & 1) ? P.nx - 1 : 0) + d : i;
+      y[k] = xs ? i : ((side & 1) ? P.ny - 1 : 0) + d;
+    }
+    const double t0 = node_value(P, f, T, x[0], y[0], 1), t1 = node_value(P, f, T, x[1], y[1], 1),
+                 t2 = node_value(P, f, T, x[2], y[2], 1);
+    const double rho = node_value(P, f, T, x[0], y[0], 0);
+    const double lam = (double)P.lam_v + (double)P.dlam * (rho - (double)P.rho_v);
+    const double dTdn = 0.5 * (-3.0 * t0 + 4.0 * t1 - t2);  // inward normal derivative
+    acc += -lam * dTdn;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppl_wall_heat_flux(ppl_t *h, int side, double *q) {
+  if (!h || !q || side < 0 || side > 3 || is_tangent(h->prec)) return PPL_E_INVAL;
+  if (h->cfg.hydro_bc[side] == PPL_PERIODIC && h->cfg.thermal_bc[side] == PPL_T_PERIODIC) return PPL_E_INVAL;
+  const int len = side < 2 ? h->ny : h->nx;
+  if ((side < 2 ? h->nx : h->ny) < 3) return PPL_E_INVAL;
+  const int nblk = (len + 255) / 256 < h->stats_blocks ? (len + 255) / 256 : h->stats_blocks;
+  if (h->prec == PPL_FP64)
+    wall_flux_partials<double><<<nblk, 256, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur],
+                                                            (const double *)h->T[h->cur], side, h->partials);
+  else
+    wall_flux_partials<float><<<nblk, 256, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur],
+                                                           (const float *)h->T[h->cur], side, h->partials);
+  CK(cudaGetLastError());
+  sum_finalize<<<1, 32, 0, h->stream>>>(h->partials, nblk, h->norm_out);
+  CK(cudaGetLastError());
+  double out = 0.0;
+  CK(cudaMemcpyAsync(&out, h->norm_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *q = out / len;
+  return PPL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Contact angle of a droplet on a wall (Sec. 4.3.1), from a host density field
+// ---------------------------------------------------------------------------------
+namespace {
+
+// first crossing of `level` walking from index 0 along a strided profile; NaN if none
+double first_crossing(const double *v, long long stride, int n, double level) {
+  for (int i = 0; i + 1 < n; ++i) {
+    const double a = v[(long long)i * stride], b = v[(long long)(i + 1) * stride];
+    if ((a - level) * (b - level) <= 0.0 && a != b) return i + (a - level) / (a - b);
+  }
+  return std::nan("");
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppl_contact_angle(const double *rho, int32_t nx, int32_t ny, int side, double rho_mid, double *theta) {
+  if (!rho || !theta || nx < 3 || ny < 3 || side < 0 || side > 3) return PPL_E_INVAL;
+  // walk the wall line (index s) and the inward direction (index n) with strides
+  const bool xs = side < 2;
+  const int L = xs ? ny : nx, D = xs ? nx : ny;
+  const long long s_stride = xs ? nx : 1;
+  const long long n_stride = (xs ? 1 : (long long)nx) * ((side & 1) ? -1 : 1);
+  const long long origin = (side & 1) ? (xs ? nx - 1 : (long long)(ny - 1) * nx) : 0;
+  // base line: the first line from the wall inward whose densest node is liquid with a
+  // crossing on each side (a density layer on the wall line can hide the foot there)
+  for (int n0 = 0; n0 < D / 2; ++n0) {
+    const double *line = rho + origin + n0 * n_stride;
+    int cx = 0;
+    for (int s = 1; s < L; ++s)
+      if (line[s * s_stride] > line[cx * s_stride]) cx = s;
+    if (!(line[cx * s_stride] > rho_mid)) continue;
+    const double *foot = line + cx * s_stride;
+    const double right = cx + first_crossing(foot, s_stride, L - cx, rho_mid);
+    const double left = cx - first_crossing(foot, -s_stride, cx + 1, rho_mid);
+    if (!std::isfinite(right) || !std::isfinite(left)) continue;
+    const double a = 0.5 * (right - left);
+    const int centre = (int)std::lround(0.5 * (right + left));
+    if (centre < 0 || centre >= L) return PPL_E_INVAL;
+    const double up = first_crossing(line + centre * s_stride, n_stride, D - n0, rho_mid);
+    if (!std::isfinite(up) || !(up > 0.0)) return PPL_E_INVAL;
+    // circle through (+-a, n0) and (0, n0 + up); its centre sits at height h - Rc
+    const double Rc = (a * a + up * up) / (2.0 * up);
+    const double yc = n0 + up - Rc;
+    const double q = std::fmax(-1.0, std::fmin(1.0, yc / Rc));
+    *theta = 90.0 + std::asin(q) * (180.0 / 3.14159265358979323846);
+    return PPL_OK;
+  }
+  return PPL_E_INVAL;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Time-shift search of Eq. (rel-diff-minimize)
+// ---------------------------------------------------------------------------------
+extern "C" {
+
+int ppl_time_shift(ppl_t *coarse, const ppl_t *finest, int field, int64_t m, int64_t stride, int64_t *delta,
+                   double *num_min) {
+  if (!coarse || !finest || !delta || (field != 0 && field != 1) || m < 0 || stride < 1) return PPL_E_INVAL;
+  for (int s = 0; s < 4; ++s)
+    if (coarse->cfg.hydro_bc[s] != finest->cfg.hydro_bc[s]) return PPL_E_INVAL;
+  int64_t best_d = 0;
+  double best = -1.0;
+  for (int64_t d = -m; d <= m; d += stride) {
+    double num = 0.0, den = 0.0;
+    int rc = ppl_cross_norm(coarse, finest, field, &num, &den);
+    if (rc) return rc;
+    if (best < 0.0 || num < best) {
+      best = num;
+      best_d = d;
+    }
+    if (d + stride <= m) {
+      rc = ppl_step(coarse, stride);
+      if (rc) return rc;
+    }
+  }
+  *delta = best_d;
+  if (num_min) *num_min = best;
+  return PPL_OK;
 }
 
 }  // extern "C"

@@ -74,7 +74,9 @@ __device__ __forceinline__ double line_weight(int g, int n, int bc_lo, int bc_hi
 template <typename real>
 __device__ __forceinline__ void cp_async_real(real *smem_dst, const real *gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  if (sizeof(real) == 8)
+  if (sizeof(real) == 16)  // value + tangent of the sensitivity step
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else if (sizeof(real) == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
@@ -227,23 +229,32 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
           const real qxy = twelfth * (p5 - p6 + p7 - p8);
           const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
           if (ws >= 0) {
-            // solid links (psi = 0 in the ring) carry psi_w = psi(rho_w, T) (Eqs. shanchen-walls,
-            // psi-based-formula, Q-psi-based): their force weights sum to 1/2 along the outward
-            // normal; in Q they add (1/2, 1/6) psi_w to the normal and tangential components
-            const real argw = psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]);
-            if (!(argw >= real(0))) flags |= FLAG_PSI_NEG;
-            const real psi_w = sqrt(fmax(argw, real(0)));
-            const real hw = real(0.5) * psi_w;
+            // solid links (psi = 0 in the ring): their force weights sum to 1/2 along the
+            // outward normal; in Q they add (1/2, 1/6) times the link's psi to the normal and
+            // tangential components. psi-based model (Eqs. shanchen-walls, psi-based-formula,
+            // Q-psi-based): both use psi_w = psi(rho_w, T). Modified model (Eqs.
+            // mod-psi-based-formula, Q-mod-psi-based): the force is -G_w psi^2 sum w c, i.e.
+            // a link psi of (G_w / G) psi, and Q drops the links (link psi = psi).
+            real pf, pq;
+            if (P.mod_psi) {
+              pf = P.Gw_over_G * psi_c;
+              pq = psi_c;
+            } else {
+              const real argw = psi_arg(P, wall_rho_w(P, ws, cm.src, rm.src), P.T_ref + rT[i0]);
+              if (!(argw >= real(0))) flags |= FLAG_PSI_NEG;
+              pf = pq = sqrt(fmax(argw, real(0)));
+            }
+            const real hw = real(0.5) * pf;
             if (ws == 0) sx -= hw;
             else if (ws == 1) sx += hw;
             else if (ws == 2) sy -= hw;
             else sy += hw;
             if (ws < 2) {
-              qxx += hw;
-              qyy += (real(1) / real(6)) * psi_w;
+              qxx += real(0.5) * pq;
+              qyy += (real(1) / real(6)) * pq;
             } else {
-              qxx += (real(1) / real(6)) * psi_w;
-              qyy += hw;
+              qxx += (real(1) / real(6)) * pq;
+              qyy += real(0.5) * pq;
             }
           }
           const real qf = P.kappa_G2 * psi_c;
@@ -422,7 +433,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
           flags |= (rho_new == rho_new && fabs(T_new) <= big && rho_new <= big) ? FLAG_RHO_NONPOS : FLAG_NAN;
         const real wr = (!SIMPLE && any_outflow) ? real(wcol * line_weight(r, P.ny, P.hbc[2], P.hbc[3]))
                                                  : (any_outflow ? real(wcol) : real(1));
-        if (sizeof(real) == 8) {
+        if (sizeof(real) != 4) {
           acc += double(wr * rho_new);
         } else {
           // compensated FP32 sum of this thread's column (FP64 beyond the thread)

@@ -9,6 +9,8 @@ constexpr int kNT32 = 128;  // threads (columns incl. the 3 + 3 halo) per CTA, F
 constexpr int kPF32 = 1;    // rows staged ahead, FP32
 constexpr int kNT64 = 128;
 constexpr int kPF64 = 1;
+constexpr int kNTD = 128;  // tangent (Dual) step
+constexpr int kPFD = 1;
 
 struct StepVariant {
   int nt;        // threads per CTA = strip width incl. halo
@@ -18,5 +20,6 @@ struct StepVariant {
 
 StepVariant step_variant_fp32();
 StepVariant step_variant_fp64();
+StepVariant step_variant_tangent();  // FP64 value + derivative (Dual)
 
 }  // namespace ppl_dev

@@ -217,12 +217,32 @@ int ppl_refine(const ppl_config *base, int32_t n_base, int32_t n, double T_ratio
   const double tsc = ppl_tc(c.a, c.b, c.R) / ppl_tc(base->a, base->b, base->R);
   for (int s = 0; s < 4; ++s) c.T_side[s] = base->T_side[s] * tsc;
   c.T_ref = base->T_ref * tsc;
+  c.iso_steps = (int64_t)std::llround((double)base->iso_steps * r * r);  // dt ~ dx^2
   c.gx = base->gx / (r * r * r);
   c.gy = base->gy / (r * r * r);
   const double T = T_ratio * ppl_tc(c.a, c.b, c.R);
   if (ppl_sigma_for(c.a, c.b, c.R, c.omega, c.G, T, &c.sigma)) return PPL_E_INVAL;
   if (ppl_kappa_for(base->a, n_base, n, c.b, c.R, c.omega, c.G, T_ratio, base->kappa, &c.kappa)) return PPL_E_INVAL;
   *out = c;
+  return PPL_OK;
+}
+
+
+int ppl_pressure(double a, double b, double R, double omega, double T, double rho, double *p, double *dp_drho) {
+  Pr e;
+  if (!(a > 0) || !(b > 0) || !(R > 0) || !(T > 0) || !(rho >= 0) || !(b * rho < 1.0)) return PPL_E_INVAL;
+  e.a = a;
+  e.b = b;
+  e.R = R;
+  e.omega = omega;
+  e.G = -1.0;
+  e.T = T;
+  e.Tc = ppl_tc(a, b, R);
+  e.k = 0.37464 + 1.54226 * omega - 0.2699 * omega * omega;
+  const double ar = 1.0 + e.k * (1.0 - std::sqrt(T / e.Tc));
+  e.aa = a * ar * ar;
+  if (p) *p = e.p(rho);
+  if (dp_drho) *dp_drho = e.dp(rho);
   return PPL_OK;
 }
 

@@ -15,6 +15,9 @@ from . import build as _build
 
 PPL_OK, PPL_E_INVAL, PPL_E_CUDA, PPL_E_NUMERIC, PPL_E_TIMEOUT, PPL_E_IO, PPL_E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 PPL_FP64, PPL_FP32DEV = 0, 1
+PPL_FP64_DSIGMA, PPL_FP64_DKAPPA = 2, 3  # FP64 state + its derivative w.r.t. sigma / kappa
+PRECISIONS = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV, "fp64_dsigma": PPL_FP64_DSIGMA,
+              "fp64_dkappa": PPL_FP64_DKAPPA}
 FLAG_PSI_NEG, FLAG_NAN, FLAG_RHO_NONPOS = 1, 2, 4
 
 _D = ctypes.c_double
@@ -86,6 +89,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_fields_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int]
     L.ppl_populations.argtypes = [H, _PD]
+    L.ppl_tangent_fields.argtypes = [H, _PD, _PD, _PD, _PD]
+    L.ppl_tangent_fields.restype = ctypes.c_int
     L.ppl_norms.argtypes = [H, ctypes.POINTER(PplNorms)]
     L.ppl_save.argtypes = [H, ctypes.c_char_p]
     L.ppl_load.argtypes = [H, ctypes.c_char_p]
@@ -106,6 +111,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_refine.argtypes = [ctypes.POINTER(PplConfig), ctypes.c_int32, ctypes.c_int32, _D, ctypes.POINTER(PplConfig)]
     for name in ("ppl_sigma_for", "ppl_gamma_planar", "ppl_kappa_for", "ppl_refine"):
         getattr(L, name).restype = ctypes.c_int
+    L.ppl_pressure.argtypes = [_D] * 6 + [_PD, _PD]
+    L.ppl_pressure.restype = ctypes.c_int
     L.ppl_refine_a.argtypes = [_D, ctypes.c_int32, ctypes.c_int32]
     L.ppl_refine_a.restype = _D
     L.ppl_cross_norm.argtypes = [H, H, ctypes.c_int, _PD, _PD]
@@ -117,6 +124,15 @@ def load_library(build_if_missing: bool = True):
     L.ppl_set_launch.argtypes = [H, ctypes.c_int32]
     L.ppl_get_launch.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     L.ppl_autotune.argtypes = [H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _PD]
+    L.ppl_phase_area.argtypes = [H, _D, _D, _PD]
+    L.ppl_relative_change.argtypes = [_PD, _PD, ctypes.c_int64, _PD]
+    L.ppl_wall_heat_flux.argtypes = [H, ctypes.c_int, _PD]
+    L.ppl_contact_angle.argtypes = [_PD, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, _D, _PD]
+    L.ppl_time_shift.argtypes = [H, H, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64), _PD]
+    L.ppl_time_shift.restype = ctypes.c_int
+    for name in ("ppl_phase_area", "ppl_relative_change", "ppl_wall_heat_flux", "ppl_contact_angle"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("ppl_init", "ppl_reset", "ppl_set_stream", "ppl_step", "ppl_step_async", "ppl_sync",
                  "ppl_fields", "ppl_fields_device", "ppl_populations", "ppl_norms", "ppl_save", "ppl_load",
                  "ppl_maxwell", "ppl_cross_norm", "ppl_batch_create", "ppl_batch_step", "ppl_set_launch",
@@ -142,6 +158,13 @@ def maxwell(a: float, b: float, R: float, omega: float, T: float):
     _check(load_library().ppl_maxwell(a, b, R, omega, T, ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps)),
            "ppl_maxwell")
     return rv.value, rl.value, ps.value
+
+
+def pressure(a, b, R, omega, T, rho):
+    """(p, dp/drho) of the Peng-Robinson EOS (ppl_pressure)."""
+    p, dp = _D(), _D()
+    _check(load_library().ppl_pressure(a, b, R, omega, T, rho, ctypes.byref(p), ctypes.byref(dp)), "ppl_pressure")
+    return p.value, dp.value
 
 
 def refine_a(a_base: float, n_base: int, n: int) -> float:
@@ -178,6 +201,7 @@ def refine(cfg: dict, n_base: int, n: int, T_ratio: float) -> dict:
     _check(load_library().ppl_refine(ctypes.byref(C), n_base, n, T_ratio, ctypes.byref(O)), "ppl_refine")
     out = dict(cfg)
     out.update(nx=O.nx, ny=O.ny, a=O.a, sigma=O.sigma, kappa=O.kappa, gx=O.gx, gy=O.gy, T_ref=O.T_ref,
+               iso_steps=O.iso_steps,
                T_side=[O.T_side[i] for i in range(4)])
     return out
 
@@ -192,7 +216,7 @@ def make_config(cfg: dict):
     keep = []
     C.nx, C.ny = int(cfg["nx"]), int(cfg["ny"])
     prec = cfg.get("precision", "fp64")
-    C.precision = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV}[prec] if isinstance(prec, str) else int(prec)
+    C.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     C.rho_ref = float(cfg.get("rho_ref", 1.0))
     C.T_ref = float(cfg.get("T_ref", 0.0))
     for k in ("a", "b", "R", "omega", "G", "eta_l", "eta_v", "rho_l", "rho_v", "sigma", "kappa", "gx", "gy",
@@ -215,7 +239,7 @@ def make_config(cfg: dict):
                 a = np.ascontiguousarray(arr, dtype=dt)
                 keep.append(a)
                 getattr(C, name)[sd] = a.ctypes.data_as(ptr)
-    C.contact_model = 0
+    C.contact_model = int(cfg.get("contact_model", 0))
     C.G_w = float(cfg.get("G_w", 0.0))
     return C, keep
 
@@ -278,6 +302,12 @@ class Simulation:
                "ppl_fields_device")
         return dict(zip(("rho", "ux", "uy", "T"), out))
 
+    def tangent_fields(self):
+        """d(rho, u_x, u_y, T)/d(parameter) of a fp64_dsigma / fp64_dkappa simulation."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(self.lib.ppl_tangent_fields(self.h, *[_ptr(a) for a in out]), "ppl_tangent_fields")
+        return dict(zip(("rho", "ux", "uy", "T"), out))
+
     def populations(self):
         f = np.empty((9, self.ny, self.nx))
         _check(self.lib.ppl_populations(self.h, _ptr(f)), "ppl_populations")
@@ -297,6 +327,18 @@ class Simulation:
     @property
     def launch_count(self) -> int:
         return int(self.lib.ppl_launch_count(self.h))
+
+    def phase_area(self, rho_lo: float, rho_hi: float) -> float:
+        """Liquid area in nodes: sum of clamp((rho - rho_lo) / (rho_hi - rho_lo), 0, 1)."""
+        a = ctypes.c_double()
+        _check(self.lib.ppl_phase_area(self.h, float(rho_lo), float(rho_hi), ctypes.byref(a)), "ppl_phase_area")
+        return a.value
+
+    def wall_heat_flux(self, side: int) -> float:
+        """Mean heat flux entering through boundary line `side` (Eq. pool-heat-flux)."""
+        q = ctypes.c_double()
+        _check(self.lib.ppl_wall_heat_flux(self.h, int(side), ctypes.byref(q)), "ppl_wall_heat_flux")
+        return q.value
 
     def set_launch(self, rows_per_cta: int = 0):
         """Rows per CTA of the step kernel (0 = default shape)."""
@@ -375,3 +417,33 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def relative_change(R, R_star) -> float:
+    """Eq. (relative-change-R) of two equally sampled series (the library's host routine)."""
+    a = np.ascontiguousarray(R, dtype=np.float64)
+    b = np.ascontiguousarray(R_star, dtype=np.float64)
+    if a.shape != b.shape or a.ndim != 1:
+        raise ValueError("two 1-D series of one length")
+    out = ctypes.c_double()
+    _check(load_library().ppl_relative_change(_ptr(a), _ptr(b), len(a), ctypes.byref(out)), "ppl_relative_change")
+    return out.value
+
+
+def contact_angle(rho, side: int, rho_mid: float) -> float:
+    """Contact angle in degrees of a droplet on boundary line `side` of a host density field
+    (the library's host routine, ppl_contact_angle)."""
+    a = np.ascontiguousarray(rho, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(load_library().ppl_contact_angle(_ptr(a), a.shape[1], a.shape[0], int(side), float(rho_mid),
+                                            ctypes.byref(out)), "ppl_contact_angle")
+    return out.value
+
+
+def time_shift(coarse: Simulation, finest: Simulation, m: int, stride: int, field: str = "rho"):
+    """Eq. (rel-diff-minimize): (delta, minimum numerator) with `coarse` at tau - m and
+    `finest` at tau; advances `coarse` through the search window (ppl_time_shift)."""
+    d, num = ctypes.c_int64(), ctypes.c_double()
+    _check(coarse.lib.ppl_time_shift(coarse.h, finest.h, {"rho": 0, "T": 1}[field], int(m), int(stride),
+                                     ctypes.byref(d), ctypes.byref(num)), "ppl_time_shift")
+    return d.value, num.value

@@ -1,0 +1,286 @@
+"""Mesh-refinement studies of Secs. 3-4, driven entirely through the C ABI.
+
+Each study builds the problem on a sequence of meshes with the refinement procedure of
+Sec. 3 (``ppl_refine``: a ~ dx^2, T ~ T_c, g ~ dx^3, sigma and kappa re-tuned per mesh,
+dt ~ dx^2), advances all meshes together as one batch (``ppl_batch_*``: mesh k takes
+(n_k / n_0)^2 steps per coarse step, the grids run as concurrent branches of one CUDA
+graph, each with its autotuned launch shape) and evaluates the paper's cross-mesh
+measures with the library's reductions: the droplet radius R(t) and Eq. (relative-change-R)
+(Sec. 4.1, Table 2), the contact angle and the relative change of the density fields
+(Sec. 4.3.1), the space-time differences d^N and D^N of Eqs. (rel-diff-timestep) and
+(global-rel-diff), the heat flux Q(t) of Eq. (pool-heat-flux) and the time shift of
+Eq. (rel-diff-minimize) (Sec. 4.3.2). Host code here only schedules calls and converts
+units (lengths and times to the coarsest mesh's).
+"""
+from __future__ import annotations
+
+import math
+import time
+from fractions import Fraction
+
+import numpy as np
+
+import workloads as W
+
+from . import ppl
+
+# Peng-Robinson constants of the paper's base mesh (Sec. 3.2, reading a = 3/49)
+EOS = dict(a=3.0 / 49.0, b=2.0 / 21.0, R=1.0, omega=0.344, G=-1.0)
+
+
+def substeps(meshes, base):
+    """Smallest integer steps per outer step with dt ~ dx^2: mesh n takes (n / base)^2 times
+    as many steps as the base mesh."""
+    ratios = [Fraction(n, base) ** 2 for n in meshes]
+    outer = 1
+    for r in ratios:
+        outer = outer * r.denominator // math.gcd(outer, r.denominator)
+    return [int(r * outer) for r in ratios]
+
+
+def coexistence(T_ratio):
+    Tc = ppl.tc(EOS["a"], EOS["b"], EOS["R"])
+    rv, rl, _ = ppl.maxwell(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], T_ratio * Tc)
+    return Tc, rv, rl
+
+
+def _refined(base_cfg, n_base, n, T_ratio):
+    c = ppl.refine(base_cfg, n_base, n, T_ratio)
+    return c, ppl.tc(c["a"], c["b"], c["R"])
+
+
+def _angle(rho, mid):
+    # 0 for a liquid film over the whole bottom wall (no base to read), else NaN if no cap
+    try:
+        return ppl.contact_angle(rho, 2, mid)
+    except ppl.PplError:
+        return 0.0 if float(np.min(rho[0, :])) > mid else float("nan")
+
+
+def _batch(sims, subs, autotune_steps):
+    shapes = []
+    for s in sims:
+        shapes.append(s.autotune(autotune_steps)[0] if autotune_steps else s.launch()[0])
+    return ppl.Batch(sims, subs), shapes
+
+
+def droplet_vaporization_study(meshes=(128, 256, 512), R0=20.0, T_ratio=0.8, Tv_ratio=0.9, lam=0.25,
+                               kappa=0.3, iso_steps=10000, coarse_steps=200000, sample_every=None,
+                               width=3.0, precision="fp32", autotune_steps=64):
+    """Sec. 4.1: a droplet (radius R0 on the first mesh) in vapour held at Tv on the boundary
+    ring. Returns R(t) per mesh in first-mesh lengths, sampled every outer step, Eq.
+    (relative-change-R) between successive meshes, and the slope of R^2(t) over the
+    evaporation phase (the D^2 law)."""
+    base_n = meshes[0]
+    Tc, rv, rl = coexistence(T_ratio)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], T_ratio * Tc)
+    base, _ = W.droplet_vaporization(Tc, rv, rl, sigma, nx=base_n, ny=base_n, R0=R0, width=width,
+                                     T_ratio=T_ratio, Tv_ratio=Tv_ratio, kappa=kappa, iso_steps=iso_steps,
+                                     lam=lam, precision=precision)
+    subs = substeps(meshes, base_n)
+    if sample_every is not None and sample_every % subs[0]:
+        raise ValueError("sample_every must be a multiple of %d coarse steps" % subs[0])
+    sims, params = [], []
+    for n in meshes:
+        r = n / base_n
+        c, Tcn = _refined(base, base_n, n, T_ratio)
+        _, ic = W.droplet_vaporization(Tcn, rv, rl, c["sigma"], nx=n, ny=n, R0=R0 * r, width=width * r,
+                                       T_ratio=T_ratio, Tv_ratio=Tv_ratio, kappa=c["kappa"],
+                                       iso_steps=c["iso_steps"], lam=lam, precision=precision)
+        sims.append(ppl.Simulation(c, *ic))
+        params.append({"n": n, "a": c["a"], "sigma": c["sigma"], "kappa": c["kappa"], "iso_steps": c["iso_steps"]})
+    batch, shapes = _batch(sims, subs, autotune_steps)
+    per_outer = subs[0]
+    every = max(1, (sample_every or per_outer) // per_outer)
+    mid, band = 0.5 * (rv + rl), 0.05 * (rl - rv)
+    R = [[] for _ in meshes]
+    t = []
+    t0 = time.perf_counter()
+    outer = coarse_steps // per_outer
+    for k in range(1, outer + 1):
+        batch.step(1)
+        if k % every == 0:
+            t.append(k * per_outer)
+            for i, (s, n) in enumerate(zip(sims, meshes)):
+                R[i].append(math.sqrt(s.phase_area(mid - band, mid + band) / math.pi) * base_n / n)
+    wall = time.perf_counter() - t0
+    nodes = sum(n * n * s for n, s in zip(meshes, subs)) * outer
+    batch.close()
+    for s in sims:
+        s.close()
+    dR = [ppl.relative_change(R[i], R[i + 1]) for i in range(len(meshes) - 1)]
+    slopes = []
+    tt = np.asarray(t, dtype=np.float64)
+    for r in R:
+        r2 = np.asarray(r) ** 2
+        # evaporation phase: after the isothermal start, while the droplet keeps a quarter of
+        # its initial area
+        sel = (tt > iso_steps) & (r2 > 0.25 * R0 * R0)
+        slopes.append(float(np.polyfit(tt[sel], r2[sel], 1)[0]) if sel.sum() >= 3 else float("nan"))
+    return {"meshes": list(meshes), "substeps": subs, "launch_rows": shapes, "params": params, "t": t, "R": R,
+            "delta_R": dR, "orders": [math.log(dR[i] / dR[i + 1]) / math.log(meshes[i + 1] / meshes[i])
+                                      for i in range(len(dR) - 1)],
+            "d2_slope": slopes, "seconds": wall, "mlups": nodes / wall / 1e6}
+
+
+def contact_angle_study(meshes=(160, 240, 360, 540), model=W.CONTACT_PSI, value=4.0, coarse_steps=20000,
+                        R0_frac=0.2, T_ratio=0.86, precision="fp32", autotune_steps=64):
+    """Sec. 4.3.1: an isothermal droplet on the bottom wall relaxing to its static shape on
+    every mesh. Returns the contact angle per mesh and the relative change of the density
+    fields between successive meshes (Eqs. rel-diff-timestep at the final time, the
+    Delta* rho of the paper's contact-angle table). value: rho_w (psi-based) or G_w."""
+    base_n = meshes[0]
+    Tc, rv, rl = coexistence(T_ratio)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], T_ratio * Tc)
+    kw = dict(contact_model=model, rho_w=value if model == W.CONTACT_PSI else 4.0,
+              G_w=value if model == W.CONTACT_MOD_PSI else 0.0, precision=precision)
+    base, _ = W.sessile_droplet(Tc, rv, rl, sigma, nx=base_n, ny=base_n, R0=R0_frac * base_n, **kw)
+    subs = substeps(meshes, base_n)
+    sims = []
+    for n in meshes:
+        r = n / base_n
+        c, Tcn = _refined(base, base_n, n, T_ratio)
+        _, ic = W.sessile_droplet(Tcn, rv, rl, c["sigma"], nx=n, ny=n, R0=R0_frac * n, width=3.0 * r, **kw)
+        sims.append(ppl.Simulation(c, *ic))
+    batch, shapes = _batch(sims, subs, autotune_steps)
+    t0 = time.perf_counter()
+    batch.step(max(1, coarse_steps // subs[0]))
+    wall = time.perf_counter() - t0
+    mid = 0.5 * (rv + rl)
+    theta = [_angle(s.fields()["rho"], mid) for s in sims]
+    rel = []
+    for i in range(len(meshes) - 1):
+        num, den = ppl.cross_norm(sims[i], sims[i + 1], "rho")
+        rel.append(num / den)
+    batch.close()
+    for s in sims:
+        s.close()
+    return {"meshes": list(meshes), "model": "psi" if model == W.CONTACT_PSI else "mod_psi", "value": value,
+            "theta": theta, "delta_rho": rel, "launch_rows": shapes, "seconds": wall}
+
+
+def _static_angle(n, G_w, base_n, coarse_steps, T_ratio, R0_frac, precision):
+    Tc, rv, rl = coexistence(T_ratio)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], T_ratio * Tc)
+    base, _ = W.sessile_droplet(Tc, rv, rl, sigma, nx=base_n, ny=base_n, R0=R0_frac * base_n,
+                                contact_model=W.CONTACT_MOD_PSI, G_w=G_w, precision=precision)
+    c, Tcn = _refined(base, base_n, n, T_ratio)
+    _, ic = W.sessile_droplet(Tcn, rv, rl, c["sigma"], nx=n, ny=n, R0=R0_frac * n, width=3.0 * n / base_n,
+                              contact_model=W.CONTACT_MOD_PSI, G_w=G_w, precision=precision)
+    with ppl.Simulation(c, *ic) as s:
+        s.step(int(round(coarse_steps * (n / base_n) ** 2)))
+        return _angle(s.fields()["rho"], 0.5 * (rv + rl))
+
+
+def G_w_search(meshes=(160, 240, 360, 540), G_w0=-0.8, coarse_steps=20000, tol=0.5, max_iter=10,
+               T_ratio=0.86, R0_frac=0.2, precision="fp32"):
+    """Sec. 4.3.1, the paper's G_w table: the modified psi-based model does not keep its
+    contact angle under refinement; find per mesh the G_w that restores the angle (degrees)
+    of the first mesh at G_w0. The angle falls as G_w grows more negative (stronger
+    adhesion): the search brackets the target by steps of 0.05 from the previous mesh's
+    G_w, then refines by false position; each evaluation is a run to the static shape.
+    Returns the target angle and (G_w, theta, evaluations) per mesh."""
+    base_n = meshes[0]
+    target = _static_angle(base_n, G_w0, base_n, coarse_steps, T_ratio, R0_frac, precision)
+    out = [{"n": base_n, "G_w": G_w0, "theta": target, "evaluations": 1}]
+    g_prev = G_w0
+    for n in meshes[1:]:
+        evals = []
+
+        def f(g):
+            th = _static_angle(n, g, base_n, coarse_steps, T_ratio, R0_frac, precision)
+            evals.append((g, th))
+            return th - target
+
+        ga, fa = g_prev, f(g_prev)
+        step = -0.05 if fa > 0 else 0.05
+        gb, fb = ga + step, f(ga + step)
+        while math.isfinite(fa + fb) and fa * fb > 0 and len(evals) < max_iter:
+            ga, fa = gb, fb
+            gb, fb = gb + step, f(gb + step)
+        side = 0
+        while math.isfinite(fa + fb) and fa * fb <= 0 and len(evals) < max_iter and min(abs(fa), abs(fb)) > tol:
+            gc = gb - fb * (gb - ga) / (fb - fa) if fb != fa else 0.5 * (ga + gb)
+            fc = f(gc)
+            if not math.isfinite(fc):
+                break
+            if fc * fb < 0:
+                ga, fa = gb, fb
+                side = 0
+            else:  # Illinois step: halve the kept end's value twice in a row
+                fa = 0.5 * fa if side == 1 else fa
+                side = 1
+            gb, fb = gc, fc
+        g_best, th_best = min(evals, key=lambda e: abs(e[1] - target) if math.isfinite(e[1]) else 1e9)
+        out.append({"n": n, "G_w": g_best, "theta": th_best, "evaluations": len(evals),
+                    "trace": [list(e) for e in evals]})
+        g_prev = g_best
+    return {"target_theta": target, "meshes": out}
+
+
+def pool_boiling_study(meshes=(160, 240, 360, 540), rho_wh=3.44, Th_ratio=1.2, coarse_steps=40000,
+                       sample_every=320, tau=5120, m=4800, shift_stride=160, precision="fp32",
+                       autotune_steps=64):
+    """Sec. 4.3.2 with the paper's settings (walls at T_sat = 0.86 T_c, heater of a fifth of
+    the width at Th, rho_w 6.50 / rho_wh / 0.38, liquid below half height, g = -2.5e-5 on
+    the first mesh). Returns d^N(t) of rho and T between successive meshes at the output
+    times (temperature as T / T_c of each mesh), their global D^N, the bottom-wall heat
+    flux Q(t) per mesh (in first-mesh units), and the time shift
+    delta of each coarser mesh against the finest at tau (Eq. rel-diff-minimize, search
+    window +-m, all in first-mesh steps)."""
+    base_n = meshes[0]
+    T_ratio = 0.86
+    Tc, rv, rl = coexistence(T_ratio)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], T_ratio * Tc)
+    subs = substeps(meshes, base_n)
+    if sample_every % subs[0] or tau % subs[0]:
+        raise ValueError("sample_every and tau must be multiples of %d coarse steps" % subs[0])
+
+    def build(n):
+        proto, _ = W.paper_pool_boiling(Tc, rv, rl, sigma, n=base_n, rho_wh=rho_wh, Th_ratio=Th_ratio,
+                                        precision=precision, per_node=False)
+        c, Tcn = _refined(proto, base_n, n, T_ratio)
+        cfg, ic = W.paper_pool_boiling(Tcn, rv, rl, c["sigma"], n=n, rho_wh=rho_wh, Th_ratio=Th_ratio,
+                                       g=-c["gy"], precision=precision)
+        cfg.update(a=c["a"], kappa=c["kappa"])
+        return cfg, ic
+
+    cases = [build(n) for n in meshes]
+    sims = [ppl.Simulation(c, *ic) for c, ic in cases]
+    batch, shapes = _batch(sims, subs, autotune_steps)
+    every = sample_every // subs[0]
+    terms = {f: [[] for _ in meshes[1:]] for f in ("rho", "T")}
+    Q = [[] for _ in meshes]
+    t = []
+    t0 = time.perf_counter()
+    for k in range(1, coarse_steps // subs[0] + 1):
+        batch.step(1)
+        if k % every == 0:
+            t.append(k * subs[0])
+            for i in range(len(meshes) - 1):
+                for f in ("rho", "T"):
+                    terms[f][i].append(ppl.cross_norm(sims[i], sims[i + 1], f))
+            for i, s in enumerate(sims):
+                Q[i].append(s.wall_heat_flux(2))
+    wall = time.perf_counter() - t0
+    batch.close()
+    for s in sims:
+        s.close()
+    d = {f: [[a / b for a, b in pairs] for pairs in terms[f]] for f in terms}
+    D = {f: [sum(a for a, _ in pairs) / sum(b for _, b in pairs) for pairs in terms[f]] for f in terms}
+
+    # time shifts against the finest mesh at tau
+    cf, icf = cases[-1]
+    shifts = []
+    with ppl.Simulation(cf, *icf) as finest:
+        finest.step(tau * subs[-1] // subs[0])
+        for (c, ic), n, sub in zip(cases[:-1], meshes[:-1], subs[:-1]):
+            scale = sub / subs[0]
+            with ppl.Simulation(c, *ic) as s:
+                s.step(int(round((tau - m) * scale)))
+                delta, num = ppl.time_shift(s, finest, int(round(m * scale)), int(round(shift_stride * scale)))
+                shifts.append({"n": n, "delta": delta / scale, "num": num})
+    # Q in first-mesh units: T scales with dx^2 (Table 1) and the wall gradient with 1/dx
+    Q = [[q * (n / base_n) ** 3 for q in series] for series, n in zip(Q, meshes)]
+    return {"meshes": list(meshes), "substeps": subs, "launch_rows": shapes, "t": t, "d": d, "D": D, "Q": Q,
+            "shifts": shifts, "seconds": wall, "rho_wh": rho_wh, "Th_ratio": Th_ratio}

@@ -117,5 +117,70 @@ def test_refine_applies_table1_scaling():
     assert out["a"] == pytest.approx(3 / 49 / r ** 2, rel=1e-14)
     assert out["gy"] == pytest.approx(-2.5e-5 / r ** 3, rel=1e-14)
     assert out["T_side"][2] == pytest.approx(0.9 * Tc / r ** 2, rel=1e-12)
+    base["iso_steps"] = 10000
+    assert ppl.refine(base, 128, 192, 0.86)["iso_steps"] == 22500  # dt ~ dx^2
     assert out["sigma"] == pytest.approx(0.115, abs=5e-4)     # Table 2, L = 192
     assert 1 - out["kappa"] == pytest.approx(1 + 5.17e-2, rel=1e-2)  # Sec. 3.2
+
+
+def test_relative_change_matches_oracle():
+    # Eq. (relative-change-R), the library's host routine against the oracle's
+    import numpy as np
+    from oracle import norms
+    from paper_2201_04560_gb300 import ppl
+    rng = np.random.default_rng(2)
+    R, Rs = 20 + rng.random(300), 20 + rng.random(300)
+    assert ppl.relative_change(R, Rs) == pytest.approx(norms.relative_change_R(R, Rs), rel=1e-13)
+    with pytest.raises(ppl.PplError):
+        ppl.relative_change(R[:0], Rs[:0])
+    with pytest.raises(ppl.PplError):
+        ppl.relative_change(R[:3], np.zeros(3))
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+@pytest.mark.parametrize("yc", [-12.0, 0.0, 10.0])
+def test_contact_angle_matches_oracle_on_caps(side, yc):
+    # the library's host routine against the oracle's on a circular cap cut by a wall line,
+    # for each of the four sides (the field is rotated so that the wall is that side)
+    import numpy as np
+    from oracle import norms
+    from paper_2201_04560_gb300 import ppl
+    nx, ny, R, W = 150, 80, 28.0, 3.0
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    rho = 0.38 + 0.5 * (6.5 - 0.38) * (1 + np.tanh(2 * (R - np.hypot(x - 70.6, y - yc)) / W))
+    mid = 0.5 * (6.5 + 0.38)
+    want = norms.contact_angle(rho, mid)
+    assert want == pytest.approx(90.0 + np.degrees(np.arcsin(yc / R)), abs=1.0)
+    field = {2: rho, 3: rho[::-1, :], 0: rho.T, 1: rho.T[:, ::-1]}[side]
+    assert ppl.contact_angle(field, side, mid) == pytest.approx(want, abs=1e-9)
+
+
+def test_pressure_matches_oracle_eos():
+    from oracle import thermo
+    from paper_2201_04560_gb300 import ppl
+    e = thermo.PR()
+    for tr in (0.8, 0.86, 1.2):
+        T = tr * e.Tc
+        for rho in (0.3, 2.0, 6.5):
+            p, dp = ppl.pressure(e.a, e.b, e.R, e.omega, T, rho)
+            assert p == pytest.approx(float(e.p(rho, T)), rel=1e-13)
+            h = 1e-5
+            assert dp == pytest.approx((float(e.p(rho + h, T)) - float(e.p(rho - h, T))) / (2 * h), rel=1e-8)
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+def test_contact_angle_base_above_a_wall_layer_matches_oracle(side):
+    import numpy as np
+    from oracle import norms
+    from paper_2201_04560_gb300 import ppl
+    nx, ny, R, W, yc = 160, 90, 30.0, 3.0, -8.0
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    rho = 0.38 + 0.5 * (6.5 - 0.38) * (1 + np.tanh(2 * (R - np.hypot(x - 80.3, y - yc)) / W))
+    rho[0, :] = np.minimum(rho[0, :], 2.0)
+    mid = 0.5 * (6.5 + 0.38)
+    want = norms.contact_angle(rho, mid)
+    field = {2: rho, 3: rho[::-1, :], 0: rho.T, 1: rho.T[:, ::-1]}[side]
+    assert ppl.contact_angle(field, side, mid) == pytest.approx(want, abs=1e-9)
+    film = np.where(y < 10, 6.5, 0.38)
+    with pytest.raises(ppl.PplError):
+        ppl.contact_angle({2: film, 3: film[::-1, :], 0: film.T, 1: film.T[:, ::-1]}[side], side, mid)

@@ -176,3 +176,31 @@ def test_invalid_initial_state_is_rejected(sim_cls):
     with pytest.raises(PplError) as ei:
         sim_cls(cfg, rho, z, z, np.full((16, 16), 2.0 * e.Tc))
     assert ei.value.code == -1
+
+
+def _transpose_case(cfg, ic):
+    # the same problem with the walls on the x sides
+    c = dict(cfg)
+    c["nx"], c["ny"] = cfg["ny"], cfg["nx"]
+    c["hydro_bc"] = [cfg["hydro_bc"][2], cfg["hydro_bc"][3], cfg["hydro_bc"][0], cfg["hydro_bc"][1]]
+    c["thermal_bc"] = [cfg["thermal_bc"][2], cfg["thermal_bc"][3], cfg["thermal_bc"][0], cfg["thermal_bc"][1]]
+    c["T_side"] = [cfg["T_side"][2], cfg["T_side"][3], cfg["T_side"][0], cfg["T_side"][1]]
+    c["rho_w_side"] = [cfg["rho_w_side"][2], cfg["rho_w_side"][3], cfg["rho_w_side"][0], cfg["rho_w_side"][1]]
+    rho, ux, uy, T = ic
+    return c, (rho.T.copy(), uy.T.copy(), ux.T.copy(), T.T.copy())
+
+
+@pytest.mark.parametrize("model,axis", [("psi", "y"), ("mod_psi", "y"), ("mod_psi", "x")])
+def test_sessile_droplet_contact_models_fp64(sim_cls, th, model, axis):
+    # Eqs. (psi-based-formula) / (mod-psi-based-formula) with Eqs. (Q-psi-based) /
+    # (Q-mod-psi-based): kappa != 0 so that the wall form of Q matters
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cm = W.CONTACT_PSI if model == "psi" else W.CONTACT_MOD_PSI
+    cfg, ic = W.sessile_droplet(e.Tc, rv, rl, th["sigma086"], nx=70, ny=41, R0=13.0, contact_model=cm,
+                                rho_w=4.0, G_w=-0.8)
+    cfg.update(kappa=0.3)
+    if axis == "x":
+        cfg, ic = _transpose_case(cfg, ic)
+    got, want = run_pair(sim_cls, cfg, ic, 400)
+    assert_fp64_parity(got, want)

@@ -53,6 +53,8 @@ def test_cross_norm_matches_oracle(ppl, th, case):
     oc.step(steps[0])
     of.step(steps[1])
     foc, fof = oc.fields(), of.fields()
+    # temperatures compare as T / T_c of each mesh
+    foc["T"], fof["T"] = foc["T"] / oracle.tc(cc), fof["T"] / oracle.tc(cf)
     for field in ("rho", "T"):
         num, den = ppl.cross_norm(sc, sf, field)
         wnum, wden = norms.rel_diff_terms(foc[field], fof[field], px, py)
@@ -161,3 +163,79 @@ def test_autotune_restores_state(ppl, th):
     # gravity on: the per-CTA mass partials round differently, nothing else differs
     for k in ("rho", "T"):
         np.testing.assert_allclose(got[k], want[k], rtol=1e-12)
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_phase_area_matches_oracle(ppl, th, precision, rtol):
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.droplet_vaporization(e.Tc, rv, rl, 0.1, nx=60, ny=52, R0=12.0, iso_steps=40, precision=precision)
+    s = ppl.Simulation(cfg, *ic)
+    s.step(160)
+    o = oracle.Oracle(cfg, *ic)
+    o.step(160)
+    rho = o.fields()["rho"]
+    for lo, hi in ((rv, rl), (0.5 * (rv + rl) - 0.1, 0.5 * (rv + rl) + 0.1)):
+        assert s.phase_area(lo, hi) == pytest.approx(norms.phase_area(rho, lo, hi), rel=rtol)
+    with pytest.raises(ppl.PplError):
+        s.phase_area(rl, rv)
+    s.close()
+
+
+def test_time_shift_search(ppl, th):
+    # Eq. (rel-diff-minimize): the same mesh as "finest" has its minimum, exactly zero, at
+    # delta = 0; a finer mesh's minimum and its value agree with the oracle's scan
+    (cc, icc), (cf, icf) = droplet(th, 40, kappa=0.2), droplet(th, 61, kappa=0.2)
+    tau, m, stride = 60, 30, 10
+    fine = ppl.Simulation(cc, *icc)
+    fine.step(tau)
+    c = ppl.Simulation(cc, *icc)
+    c.step(tau - m)
+    d, num = ppl.time_shift(c, fine, m, stride)
+    assert (d, num) == (0, 0.0)
+    c.close()
+    fine.close()
+
+    fine = ppl.Simulation(cf, *icf)
+    fine.step(tau)
+    c = ppl.Simulation(cc, *icc)
+    c.step(tau - m)
+    d, num = ppl.time_shift(c, fine, m, stride)
+    of = oracle.Oracle(cf, *icf)
+    of.step(tau)
+    ff = of.fields()["rho"]
+    oc = oracle.Oracle(cc, *icc)
+    oc.step(tau - m)
+    scan = []
+    for k, shift in enumerate(range(-m, m + 1, stride)):
+        if k:
+            oc.step(stride)
+        scan.append((norms.rel_diff_terms(oc.fields()["rho"], ff, True, True)[0], shift))
+    wnum, wd = min(scan)
+    assert d == wd
+    assert num == pytest.approx(wnum, rel=1e-8)
+    c.close()
+    fine.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-9), ("fp32", 2e-3)])
+def test_wall_heat_flux_matches_oracle(ppl, th, precision, rtol):
+    # Eq. (pool-heat-flux) through the heated bottom wall and the adiabatic top wall
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=64, ny=48, g=3e-5, precision=precision)
+    s = ppl.Simulation(cfg, *ic)
+    s.step(120)
+    o = oracle.Oracle(cfg, *ic)
+    o.step(120)
+    fo = o.fields()
+    for side in (2, 3):
+        want = norms.wall_heat_flux(fo["rho"], fo["T"], side, cfg["rho_v"], cfg["rho_l"], cfg["lambda_v"],
+                                    cfg["lambda_l"])
+        scale = abs(norms.wall_heat_flux(fo["rho"], fo["T"], 2, cfg["rho_v"], cfg["rho_l"], cfg["lambda_v"],
+                                         cfg["lambda_l"]))
+        assert s.wall_heat_flux(side) == pytest.approx(want, rel=rtol, abs=rtol * scale)
+    assert s.wall_heat_flux(2) > 0  # the heater feeds heat into the pool
+    with pytest.raises(ppl.PplError):
+        s.wall_heat_flux(0)  # periodic side
+    s.close()

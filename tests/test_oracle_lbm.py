@@ -319,3 +319,51 @@ def test_window_step_reproduces_the_full_domain(steps, g):
         xs = np.arange(x0, x1) % 40
         np.testing.assert_allclose(f, full.f[:, y0:y1][:, :, xs], rtol=1e-12, atol=1e-14)
         np.testing.assert_allclose(T, full.T[y0:y1][:, xs], rtol=1e-12, atol=0)
+
+
+def _smooth_wall_state(nx, ny, rv, rl, T0, seed):
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    rho = 0.5 * (rl + rv) + 0.45 * (rl - rv) * np.sin(2 * np.pi * x / nx + rng.random()) * np.cos(np.pi * y / ny)
+    T = T0 * (1.0 + 0.02 * np.cos(2 * np.pi * y / ny + rng.random()))
+    ux = 0.01 * np.sin(2 * np.pi * y / ny)
+    uy = 0.01 * np.cos(2 * np.pi * x / nx)
+    return rho, ux, uy, T
+
+
+@pytest.mark.parametrize("axis", ["y", "x"])
+def test_modified_psi_model_reduces_to_psi_based(pr08, axis):
+    # Eq. (mod-psi-based-formula) with G_w = G gives the force of Eq. (psi-based-formula)
+    # when psi_w = psi(x), i.e. rho_w(x) equal to the wall node's own density (same T), and
+    # Eq. (Q-mod-psi-based) equals Eq. (Q-psi-based) then (psi_w - psi = 0 on solid links).
+    # With G_w = 0 and kappa = 0 it equals the psi-based model with rho_w = 0 (psi_w = 0).
+    e, T, rv, rl = pr08
+    nx, ny = (10, 14) if axis == "y" else (14, 10)
+    rho, ux, uy, T0 = _smooth_wall_state(nx, ny, rv, rl, T, 4)
+    if axis == "x":
+        rho, ux, uy, T0 = rho.T.copy(), uy.T.copy(), ux.T.copy(), T0.T.copy()
+        nx, ny = ny, nx
+    hb = [W.PERIODIC, W.PERIODIC, W.WALL, W.WALL] if axis == "y" else [W.WALL, W.WALL, W.PERIODIC, W.PERIODIC]
+    base = W.base_config(nx, ny, sigma=0.1, kappa=0.4, hydro_bc=hb, s=W.RATES_STEFAN_POOL)
+    lines = ([rho[0, :], rho[-1, :]] if axis == "y" else [rho[:, 0], rho[:, -1]])
+    rho_w = [None] * 4
+    lo, hi = (2, 3) if axis == "y" else (0, 1)
+    rho_w[lo], rho_w[hi] = lines[0].copy(), lines[1].copy()
+    ic = (rho, ux, uy, T0)
+
+    a = oracle.Oracle(dict(base, rho_w=rho_w), *ic)
+    b = oracle.Oracle(dict(base, contact_model=W.CONTACT_MOD_PSI, G_w=base["G"]), *ic)
+    a.step(1)
+    b.step(1)
+    np.testing.assert_allclose(b.f, a.f, rtol=1e-13, atol=1e-15)
+
+    k0 = dict(base, kappa=0.0)
+    c = oracle.Oracle(dict(k0, rho_w_side=[0.0] * 4), *ic)
+    d = oracle.Oracle(dict(k0, contact_model=W.CONTACT_MOD_PSI, G_w=0.0), *ic)
+    c.step(1)
+    d.step(1)
+    np.testing.assert_allclose(d.f, c.f, rtol=1e-13, atol=1e-15)
+    # and the adhesion is not a no-op: another G_w changes the wall rows only at first
+    g = oracle.Oracle(dict(base, contact_model=W.CONTACT_MOD_PSI, G_w=-0.8), *ic)
+    g.step(1)
+    assert np.abs(g.f - b.f).max() > 1e-4

@@ -92,3 +92,73 @@ def test_global_difference_sums_over_times():
 
 def test_convergence_order_of_a_power_law():
     assert norms.convergence_order(3.0 * 0.1 ** 1.7, 3.0 * 0.05 ** 1.7, 0.1, 0.05) == pytest.approx(1.7)
+
+
+def test_phase_area_limits_and_disc():
+    assert norms.phase_area(np.full((5, 7), 0.3), 0.3, 6.0) == 0.0
+    assert norms.phase_area(np.full((5, 7), 6.0), 0.3, 6.0) == 35.0
+    assert norms.phase_area(np.array([[0.0, 3.15, 9.0]]), 0.3, 6.0) == pytest.approx(0.5 + 1.0)
+    # a tanh disc of radius R0 and width W: the continuum integral of the fraction
+    # 1/2 (1 + tanh(2 (R0 - d) / W)) over the plane is pi R0^2 + pi^3 W^2 / 48
+    # (the odd part cancels; the even part is (W/2)^2 * 2 * int u / (e^{2u} + 1) du)
+    n, R0, W = 96, 20.0, 3.0
+    y, x = np.mgrid[0:n, 0:n]
+    d = np.hypot(x - (n - 1) / 2, y - (n - 1) / 2)
+    rho = 0.3 + 0.5 * (6.0 - 0.3) * (1 + np.tanh(2 * (R0 - d) / W))
+    assert norms.phase_area(rho, 0.3, 6.0) == pytest.approx(np.pi * R0 ** 2 + np.pi ** 3 * W ** 2 / 48, rel=1e-4)
+
+
+def test_relative_change_hand_case():
+    assert norms.relative_change_R([1.0, 2.0, 3.0], [1.0, 2.5, 2.0]) == pytest.approx(1.5 / 5.5)
+    assert norms.relative_change_R([4.0, 4.0], [4.0, 4.0]) == 0.0
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+def test_wall_heat_flux_exact_on_quadratic_profiles(side):
+    # the one-sided difference is exact for quadratics; constant lambda at rho = rho_v
+    ny, nx = 9, 12
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    n = {0: x, 1: nx - 1 - x, 2: y, 3: ny - 1 - y}[side]  # inward distance from the side
+    T = 1.0 + 0.3 * n - 0.02 * n ** 2
+    rho = np.full((ny, nx), 0.4)
+    q = norms.wall_heat_flux(rho, T, side, 0.4, 6.0, 0.7, 3.0)
+    assert q == pytest.approx(-0.7 * 0.3, rel=1e-13)  # dT/dn = 0.3 at the line
+
+
+def test_wall_heat_flux_lambda_law_and_mean():
+    # lambda(rho) linear: at rho_l it is lambda_l; the mean runs over the line
+    ny, nx = 5, 4
+    T = np.tile(np.array([2.0, 1.0, 0.0, -1.0, -2.0])[:, None], (1, nx))  # dT/dy = -1
+    rho = np.full((ny, nx), 6.0)
+    rho[0, :2] = 0.4  # half the line at rho_v
+    q = norms.wall_heat_flux(rho, T, 2, 0.4, 6.0, 0.7, 3.0)
+    assert q == pytest.approx(0.5 * (0.7 + 3.0), rel=1e-14)
+
+
+@pytest.mark.parametrize("yc", [-15.0, 0.0, 12.0])
+def test_contact_angle_of_a_circular_cap(yc):
+    # a tanh-smoothed circle of radius 30 cut by the wall line y = 0 at height yc of its
+    # centre: theta = 90 deg + asin(yc / R) through the liquid
+    nx, ny, R, W = 160, 90, 30.0, 3.0
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    d = np.hypot(x - 80.3, y - yc)
+    rho = 0.38 + 0.5 * (6.5 - 0.38) * (1 + np.tanh(2 * (R - d) / W))
+    want = 90.0 + np.degrees(np.arcsin(yc / R))
+    assert norms.contact_angle(rho, 0.5 * (6.5 + 0.38)) == pytest.approx(want, abs=1.0)
+
+
+def test_contact_angle_with_a_depleted_wall_layer():
+    # a density layer on the wall line hides the foot there: the base is read on the first
+    # line above it and the cap is still the circle of the droplet
+    nx, ny, R, W, yc = 160, 90, 30.0, 3.0, -8.0  # theta = 74.5 deg
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    rho = 0.38 + 0.5 * (6.5 - 0.38) * (1 + np.tanh(2 * (R - np.hypot(x - 80.3, y - yc)) / W))
+    rho[0, :] = np.minimum(rho[0, :], 2.0)
+    want = 90.0 + np.degrees(np.arcsin(yc / R))
+    assert norms.contact_angle(rho, 0.5 * (6.5 + 0.38)) == pytest.approx(want, abs=1.0)
+    # a droplet that left the wall reads as 180 deg (its circle no longer reaches the wall);
+    # a liquid film over the whole wall has no base
+    d = np.hypot(x - 80.3, y - 40.0)
+    assert norms.contact_angle(0.38 + 3.06 * (1 + np.tanh(2 * (20 - d) / W)), 3.44) == 180.0
+    film = np.where(y < 10, 6.5, 0.38)
+    assert np.isnan(norms.contact_angle(film, 3.44))

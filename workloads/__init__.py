@@ -29,6 +29,7 @@ import numpy as np
 
 PERIODIC, WALL, OUTFLOW = 0, 1, 2
 T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
+CONTACT_PSI, CONTACT_MOD_PSI = 0, 1  # Eqs. (psi-based-formula), (mod-psi-based-formula)
 
 # rates of the droplet/Stefan/pool runs (Sec. 4.2 and 4.3 of the paper): rho, e, zeta, j, q, j, q, eta, eta
 RATES_STEFAN_POOL = [1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25]
@@ -47,6 +48,7 @@ def base_config(nx: int, ny: int, **kw) -> dict:
         T_side=[0.0] * 4, rho_w_side=[0.0] * 4,
         rho_w=[None] * 4, T_w=[None] * 4, T_dirichlet=[None] * 4,
         precision="fp64", rho_ref=1.0, T_ref=0.0,
+        contact_model=CONTACT_PSI, G_w=0.0,
     )
     for k, v in kw.items():
         if k not in cfg:
@@ -176,3 +178,54 @@ def random_smooth_density(nx, ny, rho_lo, rho_hi, seed, modes=3):
         acc += np.cos(2 * np.pi * kx * x / nx + ph[0]) * np.cos(2 * np.pi * ky * y / ny + ph[1])
     acc = (acc - acc.min()) / (acc.max() - acc.min())
     return rho_lo + (rho_hi - rho_lo) * acc
+
+
+def sessile_droplet(Tc, rho_v, rho_l, sigma, nx=160, ny=160, R0=None, width=3.0, T_ratio=0.86,
+                    contact_model=CONTACT_PSI, rho_w=4.0, G_w=-0.8, rho_w_top=None, precision="fp64"):
+    """Contact-angle test of Sec. 4.3.1: isothermal droplet initialised on the bottom wall
+    (centre one radius above it, so that it touches the wall), x periodic, Zou-He walls at
+    y = 0 and y = ny-1, the pool-boiling rates, eta = 0.1. contact_model CONTACT_PSI uses
+    rho_w at the bottom wall (Eq. psi-based-formula; the top wall holds rho_w_top, default
+    rho_v); CONTACT_MOD_PSI uses G_w on both walls (Eq. mod-psi-based-formula)."""
+    T = T_ratio * Tc
+    R0 = nx / 5.0 if R0 is None else R0
+    cfg = base_config(
+        nx, ny, s=list(RATES_STEFAN_POOL), eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v, sigma=sigma,
+        hydro_bc=[PERIODIC, PERIODIC, WALL, WALL],
+        thermal_bc=[T_PERIODIC, T_PERIODIC, T_ADIABATIC, T_ADIABATIC], T_side=[0.0, 0.0, T, T],
+        rho_w_side=[0.0, 0.0, rho_w, rho_v if rho_w_top is None else rho_w_top],
+        contact_model=contact_model, G_w=G_w, precision=precision, rho_ref=rho_v, T_ref=T)
+    return cfg, droplet_fields(nx, ny, R0, width, rho_l, rho_v, T, T, cx=(nx - 1) / 2.0, cy=R0)
+
+
+def paper_pool_boiling(Tc, rho_v, rho_l, sigma, n=160, rho_wh=3.44, Th_ratio=1.2, g=2.5e-5, heater_frac=0.2,
+                       width=None, precision="fp64", per_node=True):
+    """Pool boiling with the settings of the paper's refinement study (Sec. 4.3.2): n x n, x
+    periodic, Zou-He walls at y = 0 and y = n-1, both walls held at T_sat = 0.86 T_c except
+    the bottom-centre heater (heater_frac of the width) at Th_ratio T_c; rho_w 6.50 on the
+    bottom wall, rho_wh on the heater, 0.38 on the top wall; liquid below half height at
+    T_sat, at rest; gravity -g along y; c_v = 5, lambda 1.95 / 0.114, eta = 0.1, the
+    pool-boiling rates. per_node=False leaves out the heater's per-node arrays (a
+    prototype for ppl_refine, which rescales only per-side values)."""
+    T_sat = 0.86 * Tc
+    width = 3.0 * n / 160.0 if width is None else width
+    w = max(1, int(round(heater_frac * n)))
+    x0 = (n - w) // 2
+    heater = np.zeros(n, dtype=bool)
+    heater[x0:x0 + w] = True
+    cfg = base_config(
+        n, n, s=list(RATES_STEFAN_POOL), eta_l=0.1, eta_v=0.1, rho_l=rho_l, rho_v=rho_v, sigma=sigma,
+        gy=-g, cv=5.0, lambda_l=1.95, lambda_v=0.114, energy_on=1,
+        hydro_bc=[PERIODIC, PERIODIC, WALL, WALL],
+        thermal_bc=[T_PERIODIC, T_PERIODIC, T_DIRICHLET, T_DIRICHLET],
+        T_side=[0.0, 0.0, T_sat, T_sat], rho_w_side=[0.0, 0.0, 6.50, 0.38],
+        precision=precision, rho_ref=rho_v, T_ref=T_sat)
+    if per_node:
+        cfg["rho_w"] = [None, None, np.where(heater, rho_wh, 6.50).astype(np.float64), None]
+        cfg["T_w"] = [None, None, np.where(heater, Th_ratio * Tc, T_sat).astype(np.float64), None]
+    y, _ = np.mgrid[0:n, 0:n].astype(np.float64)
+    rho = _tanh_profile(rho_l, rho_v, 0.5 * n - y, width)
+    z = np.zeros((n, n))
+    T = np.full((n, n), T_sat)
+    T[0, heater] = Th_ratio * Tc
+    return cfg, (rho, z.copy(), z.copy(), T)
