@@ -291,7 +291,7 @@ def main():
         dt = max_over_ranks(dt)
         n = sim.norms()
         out[prec] = {"dt": dt, "steps": steps, "launches": launches, "clocks": clocks, "flags": n["flags"],
-                     "mass": n["mass"]}
+                     "mass": n["mass"], "kernel": sim.kernel, "rows_per_cta": sim.launch()[0]}
         if prec == "fp32" and not args.no_e2e:
             # end to end through the C ABI: pinned host inputs -> device, K steps, fields -> host
             host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory() for a in ic]
@@ -318,7 +318,8 @@ def main():
         return
     if args.precision != "both" or args.no_e2e:
         # profiling / partial runs: timing summary only
-        print(json.dumps({p: {"mlups": world * nodes * v["steps"] / v["dt"] / 1e6, "ms_per_step": v["dt"] / v["steps"] * 1e3}
+        print(json.dumps({p: {"mlups": world * nodes * v["steps"] / v["dt"] / 1e6, "ms_per_step": v["dt"] / v["steps"] * 1e3,
+                              "kernel": v["kernel"], "rows_per_cta": v["rows_per_cta"]}
                           for p, v in out.items() if p in ("fp32", "fp64")}))
         return
     f32, f64 = out["fp32"], out["fp64"]
@@ -336,7 +337,9 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "pool boiling %dx%d, FP32 populations as f - w rho_ref" % (NX, NY),
                    "grid": [NX, NY], "l2": "state (335 MB FP32, 671 MB FP64 per buffer) larger than L2",
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU",
+                   "kernel": {"fp32": f32["kernel"], "fp64": f64["kernel"]},
+                   "rows_per_cta": {"fp32": f32["rows_per_cta"], "fp64": f64["rows_per_cta"]}},
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                      "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,

@@ -363,10 +363,24 @@ int ppl_contact_angle(const double *rho, int32_t nx, int32_t ny, int side, doubl
  * summed per CTA (last-bit differences of rho_bar where gravity is on). Drops the
  * handle's captured graphs; synchronises. */
 int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
+
+/* Step kernel of an FP32 handle. PPL_KERNEL_COLUMN: one column per thread (any
+ * boundaries). PPL_KERNEL_PAIR: two adjacent columns per thread with packed f32x2
+ * arithmetic, for domains periodic in x for both the hydrodynamics and the temperature
+ * with an even nx (PPL_E_INVAL otherwise). PPL_KERNEL_AUTO (the default at ppl_init): PAIR
+ * where it applies, else COLUMN. FP64 and tangent handles always use the one-column
+ * kernel. Resets the launch shape to its default and drops captured graphs; synchronises.
+ * ppl_get_kernel returns the kernel in use. */
+#define PPL_KERNEL_AUTO 0
+#define PPL_KERNEL_COLUMN 1
+#define PPL_KERNEL_PAIR 2
+int ppl_select_kernel(ppl_t *h, int kernel);
+int ppl_get_kernel(const ppl_t *h);
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
 
-/* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256) with
- * CUDA events on the handle's stream, keeps the fastest, and restores the state, step
+/* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256), for
+ * each applicable step kernel (ppl_select_kernel), with CUDA events on the handle's
+ * stream, keeps the fastest pair, and restores the state, step
  * counter and launch count it found (the state is copied aside into temporary device
  * memory). *best_rows / *best_ms (may be NULL) receive the choice and its time per step.
  * PPL_E_NUMERIC if the handle's status already reports a numerical failure. */

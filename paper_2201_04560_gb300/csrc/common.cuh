@@ -52,9 +52,9 @@ struct StepIO {
   const void *T_in;
   void *f_out;
   void *T_out;
-  const double *stats_in;  // [0] rho_bar of this step
-  double *stats_out;       // [0] rho_bar of the next step, [1] mass
-  double *partials;        // one FP64 partial per CTA
+  const double *stats_in;  // [0] rho_bar of this step, [2] its derivative (tangent step)
+  double *stats_out;       // [0] rho_bar of the next step, [1] mass, [2] d rho_bar (tangent)
+  double *partials;        // one FP64 partial per CTA (two for the tangent step)
   unsigned *counter;       // CTAs done (reset by the last one)
   unsigned *status;        // PPL_FLAG_* bits
 };
@@ -69,12 +69,13 @@ __device__ __forceinline__ real wgt(int i) {
 }
 
 // ---- Peng-Robinson EOS (Eq. peng-robinson) and the psi argument (Eq. psi) ----
-template <typename real>
-__device__ __forceinline__ real pr_alpha_root(const Params<real> &P, real T) {
+// (PT: the parameter precision; real: the value type, PT itself or two packed FP32 lanes)
+template <typename PT, typename real>
+__device__ __forceinline__ real pr_alpha_root(const Params<PT> &P, real T) {
   return real(1) + P.k * (real(1) - sqrt(T) * P.sqrt_Tc_inv);
 }
-template <typename real>
-__device__ __forceinline__ real psi_arg(const Params<real> &P, real rho, real T) {
+template <typename PT, typename real>
+__device__ __forceinline__ real psi_arg(const Params<PT> &P, real rho, real T) {
   // p = rho R T / (1 - b rho) - a alpha rho^2 / (1 + 2 b rho - b^2 rho^2), over one denominator
   const real ar = pr_alpha_root(P, T);
   const real omb = real(1) - P.b * rho;
@@ -84,16 +85,16 @@ __device__ __forceinline__ real psi_arg(const Params<real> &P, real rho, real T)
 }
 // rho-only parts of T (dp/dT)_rho = T A(rho) + k B(rho) (1 + k(1 - sqrt(T/Tc))) sqrt(T/Tc),
 // with A = rho R / (1 - b rho) and B = a rho^2 / (1 + 2 b rho - b^2 rho^2) (one division)
-template <typename real>
-__device__ __forceinline__ void dpdT_parts(const Params<real> &P, real rho, real *A, real *B) {
+template <typename PT, typename real>
+__device__ __forceinline__ void dpdT_parts(const Params<PT> &P, real rho, real *A, real *B) {
   const real omb = real(1) - P.b * rho;
   const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
   const real inv = real(1) / (omb * den);
   *A = rho * P.R * den * inv;
   *B = P.a * rho * rho * omb * inv;
 }
-template <typename real>
-__device__ __forceinline__ real T_dpdT(const Params<real> &P, real A, real B, real T) {
+template <typename PT, typename real>
+__device__ __forceinline__ real T_dpdT(const Params<PT> &P, real A, real B, real T) {
   const real st = sqrt(T) * P.sqrt_Tc_inv;
   return T * A + P.k * B * (real(1) + P.k * (real(1) - st)) * st;
 }
@@ -245,8 +246,8 @@ __device__ __forceinline__ void zou_he(int side, real f[9], real Jx, real Jy) {
 
 // ---- MRT collision in deviation form (Eqs. collisionMRT, li_source_terms, S, C) ----
 // fd: deviations f~ on entry, post-collision deviations on exit. rho = rho_ref + sum f~.
-template <typename real>
-__device__ __forceinline__ void collide(const Params<real> &P, real fd[9], real rho, real delta, real ux,
+template <typename PT, typename real>
+__device__ __forceinline__ void collide(const Params<PT> &P, real fd[9], real rho, real delta, real ux,
                                         real uy, real Fx, real Fy, real Fm2_over_psi2, real Qxx, real Qyy,
                                         real Qxy, real s_eta) {
   // deviation moments m~ = M f~ (rows of M, Sec. 2)

@@ -50,15 +50,18 @@ __global__ void init_state(const Params<real> P, const double *rho0, const doubl
   T[k] = (real)(Tabs - (double)P.T_ref);
 }
 
-// Per-node diagnostics of the stored state, reduced per block into 7 FP64 partials:
-// sum rho, sum |rho|, sum |T|, min rho, max rho, min T, max T. Also checks that psi is
-// defined everywhere (including the wall values psi(rho_w, T)).
+// Per-node diagnostics of the stored state, reduced per block into kStats FP64 partials:
+// sum rho, sum |rho|, sum |T|, min rho, max rho, min T, max T, and the sum of d rho of a
+// tangent state. Also checks that psi is defined everywhere (including the wall values
+// psi(rho_w, T)).
+constexpr int kStats = 8;
+
 template <typename real>
 __global__ void stats_partials(const Params<real> P, const real *f, const real *T, double *part,
                                unsigned *status) {
   constexpr int NT = 256;
-  __shared__ double red[7][NT / 32];
-  double s[7] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300};
+  __shared__ double red[kStats][NT / 32];
+  double s[kStats] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300, 0.0};
   unsigned flags = 0;
   for (long long k = (long long)blockIdx.x * NT + threadIdx.x; k < P.plane; k += (long long)gridDim.x * NT) {
     const int gx = (int)(k % P.nx), gy = (int)(k / P.nx);
@@ -82,37 +85,38 @@ __global__ void stats_partials(const Params<real> P, const real *f, const real *
     s[4] = fmax(s[4], (double)rho);
     s[5] = fmin(s[5], (double)t);
     s[6] = fmax(s[6], (double)t);
+    s[7] += w * tangent_of(rho);
   }
   if (flags) atomicOr(status, flags);
+  auto is_sum = [](int j) { return j < 3 || j == 7; };
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    for (int j = 0; j < 3; ++j) s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
-    s[3] = fmin(s[3], __shfl_down_sync(0xffffffffu, s[3], o));
-    s[4] = fmax(s[4], __shfl_down_sync(0xffffffffu, s[4], o));
-    s[5] = fmin(s[5], __shfl_down_sync(0xffffffffu, s[5], o));
-    s[6] = fmax(s[6], __shfl_down_sync(0xffffffffu, s[6], o));
+    for (int j = 0; j < kStats; ++j) {
+      const double x = __shfl_down_sync(0xffffffffu, s[j], o);
+      s[j] = is_sum(j) ? s[j] + x : (j == 3 || j == 5 ? fmin(s[j], x) : fmax(s[j], x));
+    }
   }
   if ((threadIdx.x & 31) == 0)
-    for (int j = 0; j < 7; ++j) red[j][threadIdx.x >> 5] = s[j];
+    for (int j = 0; j < kStats; ++j) red[j][threadIdx.x >> 5] = s[j];
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < kStats) {
     const int j = threadIdx.x;
     double v = red[j][0];
     for (int w = 1; w < NT / 32; ++w) {
       const double x = red[j][w];
-      v = j < 3 ? v + x : (j == 3 || j == 5 ? fmin(v, x) : fmax(v, x));
+      v = is_sum(j) ? v + x : (j == 3 || j == 5 ? fmin(v, x) : fmax(v, x));
     }
-    part[(long long)blockIdx.x * 7 + j] = v;
+    part[(long long)blockIdx.x * kStats + j] = v;
   }
 }
 
 // fixed-order finalize of the partials: out = {sum rho, sum|rho|, sum|T|, min/max rho, min/max T};
-// stats[0] = rho_bar, stats[1] = mass
+// stats[0] = rho_bar, stats[1] = mass, stats[2] = d rho_bar (tangent states, else 0)
 __global__ void stats_finalize(const double *part, int nblk, double inv_nodes, double *out, double *stats) {
   if (threadIdx.x != 0) return;
-  double s[7] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300};
+  double s[kStats] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300, 0.0};
   for (int b = 0; b < nblk; ++b) {
-    const double *p = part + (long long)b * 7;
+    const double *p = part + (long long)b * kStats;
     s[0] += p[0];
     s[1] += p[1];
     s[2] += p[2];
@@ -120,11 +124,13 @@ __global__ void stats_finalize(const double *part, int nblk, double inv_nodes, d
     s[4] = fmax(s[4], p[4]);
     s[5] = fmin(s[5], p[5]);
     s[6] = fmax(s[6], p[6]);
+    s[7] += p[7];
   }
   for (int j = 0; j < 7; ++j) out[j] = s[j];
   if (stats) {
     stats[0] = s[0] * inv_nodes;
     stats[1] = s[0];
+    stats[2] = s[7] * inv_nodes;
   }
 }
 
@@ -171,7 +177,8 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
     sx += w * pn * real(kCX[q]);
     sy += w * pn * real(kCY[q]);
   }
-  const real rho_bar = (real)stats[0];
+  real rho_bar = (real)stats[0];
+  if constexpr (is_dual<real>::value) rho_bar = Dual(stats[0], stats[2]);  // with d rho_bar
   const real Fx = -P.G * psi_c * sx + P.gx * (rho - rho_bar);
   const real Fy = -P.G * psi_c * sy + P.gy * (rho - rho_bar);
   const real ux = (jx + real(0.5) * Fx) / rho, uy = (jy + real(0.5) * Fy) / rho;
@@ -224,7 +231,7 @@ struct ppl_sim {
   void *T[2] = {nullptr, nullptr};
   void *bnd = nullptr;  // device copies of the per-node boundary arrays
   double *stats[2] = {nullptr, nullptr};
-  double *partials = nullptr;  // max(#step CTAs, 7 * #stats blocks)
+  double *partials = nullptr;  // max(#step CTAs (x2 for tangents), kStats * #stats blocks)
   size_t npart = 0;            // doubles in partials
   uint64_t shape_gen = 0;      // bumped when the launch shape or partials change
   double *norm_out = nullptr;  // 7 doubles
@@ -296,6 +303,22 @@ uint64_t hash_config(const ppl_sim *h) {
 
 // FP64 state carrying d/d(sigma) or d/d(kappa)
 bool is_tangent(int prec) { return prec == PPL_FP64_DSIGMA || prec == PPL_FP64_DKAPPA; }
+
+// The two-column FP32 kernel needs x periodic for the hydrodynamics and the temperature
+// (no x-boundary columns) and an even nx (8-byte aligned column pairs that never straddle
+// the periodic seam).
+bool pair_applicable(const ppl_config &c) {
+  return c.precision == PPL_FP32DEV && c.hydro_bc[0] == PPL_PERIODIC && c.hydro_bc[1] == PPL_PERIODIC &&
+         c.thermal_bc[0] == PPL_T_PERIODIC && c.thermal_bc[1] == PPL_T_PERIODIC && c.nx % 2 == 0 && c.nx >= 8;
+}
+
+// kernel: PPL_KERNEL_AUTO, PPL_KERNEL_COLUMN or PPL_KERNEL_PAIR (checked by the caller)
+StepVariant pick_variant(const ppl_config &c, int kernel) {
+  if (c.precision == PPL_FP64) return step_variant_fp64();
+  if (c.precision != PPL_FP32DEV) return step_variant_tangent();
+  const bool pair = kernel == PPL_KERNEL_PAIR || (kernel == PPL_KERNEL_AUTO && pair_applicable(c));
+  return pair ? step_variant_fp32_pair() : step_variant_fp32();
+}
 
 int validate(const ppl_config *c) {
   if (!c) return PPL_E_INVAL;
@@ -525,7 +548,7 @@ int default_rows(const ppl_sim *h) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->var.fn[1], h->var.nt, h->var.smem);
   const int slots = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  const int strips = (h->nx + (h->var.nt - 6) - 1) / (h->var.nt - 6);
+  const int strips = (h->nx + h->var.width - 1) / h->var.width;
   int yblocks = slots / strips;
   if (yblocks < 1) yblocks = 1;
   int H = (h->ny + yblocks - 1) / yblocks;
@@ -681,25 +704,25 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PPL_E_CUDA);
   h->stream = h->own_stream;
 
-  // launch shape: strips of (nt - 6) columns, one wave of CTAs over the rows
-  h->var = h->prec == PPL_FP64      ? step_variant_fp64()
-           : h->prec == PPL_FP32DEV ? step_variant_fp32()
-                                    : step_variant_tangent();
+  // launch shape: strips of var.width columns, one wave of CTAs over the rows
+  h->var = pick_variant(h->cfg, PPL_KERNEL_AUTO);
   for (int e = 0; e < 2; ++e)
     if (cudaFuncSetAttribute(h->var.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->var.smem) !=
         cudaSuccess)
       return fail(PPL_E_CUDA);
   h->rows_per_cta = default_rows(h);
-  h->grid = dim3((h->nx + (h->var.nt - 6) - 1) / (h->var.nt - 6), (h->ny + h->rows_per_cta - 1) / h->rows_per_cta);
+  h->grid = dim3((h->nx + h->var.width - 1) / h->var.width, (h->ny + h->rows_per_cta - 1) / h->rows_per_cta);
   h->stats_blocks = 608;
   const size_t nctas = (size_t)h->grid.x * h->grid.y;
-  const size_t npart = nctas > (size_t)h->stats_blocks * 7 ? nctas : (size_t)h->stats_blocks * 7;
+  const size_t step_part = nctas * (is_tangent(h->prec) ? 2 : 1);
+  const size_t npart = std::max(step_part, (size_t)h->stats_blocks * kStats);
 
   // device buffers
   const size_t fbytes = (size_t)9 * h->N * h->rsz, tbytes = (size_t)h->N * h->rsz;
   for (int i = 0; i < 2; ++i) {
     if (cudaMalloc(&h->f[i], fbytes) != cudaSuccess || cudaMalloc(&h->T[i], tbytes) != cudaSuccess ||
-        cudaMalloc(&h->stats[i], 2 * sizeof(double)) != cudaSuccess)
+        cudaMalloc(&h->stats[i], 4 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(h->stats[i], 0, 4 * sizeof(double)) != cudaSuccess)
       return fail(PPL_E_NOMEM);
   }
   h->npart = npart;
@@ -989,7 +1012,7 @@ int noalloc_setup(double **scratch) {
   if (!g_noalloc_addr[dev]) {
     void *p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    for (const StepVariant &v : {step_variant_fp64(), step_variant_fp32()})
+    for (const StepVariant &v : {step_variant_fp64(), step_variant_fp32(), step_variant_fp32_pair()})
       for (int e = 0; e < 2; ++e)
         CK(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     g_noalloc_addr[dev] = p;
@@ -1014,14 +1037,14 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   double *scratch = nullptr;
   rc = noalloc_setup(&scratch);
   if (rc) return rc;
-  const StepVariant var = cfg->precision == PPL_FP64 ? step_variant_fp64() : step_variant_fp32();
-  // the launch shape of ppl_init: strips of (nt - 6) columns, one wave of CTAs over the rows
+  const StepVariant var = pick_variant(*cfg, PPL_KERNEL_AUTO);
+  // the launch shape of ppl_init: strips of var.width columns, one wave of CTAs over the rows
   int dev = 0, sms = 0, per_sm = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, var.fn[1], var.nt, var.smem));
   const int slots = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  const int strips = (cfg->nx + (var.nt - 6) - 1) / (var.nt - 6);
+  const int strips = (cfg->nx + var.width - 1) / var.width;
   int yblocks = slots / strips;
   if (yblocks < 1) yblocks = 1;
   int H = (cfg->ny + yblocks - 1) / yblocks;
@@ -1412,16 +1435,17 @@ void ppl_batch_destroy(ppl_batch_t *b) {
 namespace {
 
 int apply_rows(ppl_sim *h, int H) {
-  const int strips = (h->nx + (h->var.nt - 6) - 1) / (h->var.nt - 6);
+  const int strips = (h->nx + h->var.width - 1) / h->var.width;
   const dim3 grid(strips, (h->ny + H - 1) / H);
   const size_t nctas = (size_t)grid.x * grid.y;
   CK(cudaStreamSynchronize(h->stream));
-  if (nctas > h->npart) {
+  const size_t need = nctas * (is_tangent(h->prec) ? 2 : 1);
+  if (need > h->npart) {
     double *p = nullptr;
-    if (cudaMalloc(&p, nctas * sizeof(double)) != cudaSuccess) return PPL_E_NOMEM;
+    if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) return PPL_E_NOMEM;
     cudaFree(h->partials);
     h->partials = p;
-    h->npart = nctas;
+    h->npart = need;
   }
   for (int e = 0; e < 2; ++e)
     if (h->graph[e]) {
@@ -1443,6 +1467,22 @@ int ppl_set_launch(ppl_t *h, int32_t rows_per_cta) {
   return apply_rows(h, rows_per_cta == 0 ? default_rows(h) : rows_per_cta);
 }
 
+int ppl_select_kernel(ppl_t *h, int kernel) {
+  if (!h || kernel < PPL_KERNEL_AUTO || kernel > PPL_KERNEL_PAIR) return PPL_E_INVAL;
+  if (kernel == PPL_KERNEL_PAIR && !pair_applicable(h->cfg)) return PPL_E_INVAL;
+  const StepVariant v = pick_variant(h->cfg, kernel);
+  for (int e = 0; e < 2; ++e)
+    CK(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+  CK(cudaStreamSynchronize(h->stream));
+  h->var = v;
+  return apply_rows(h, default_rows(h));
+}
+
+int ppl_get_kernel(const ppl_t *h) {
+  if (!h) return PPL_E_INVAL;
+  return h->var.fn[0] == step_variant_fp32_pair().fn[0] ? PPL_KERNEL_PAIR : PPL_KERNEL_COLUMN;
+}
+
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas) {
   if (!h) return PPL_E_INVAL;
   if (rows_per_cta) *rows_per_cta = h->rows_per_cta;
@@ -1460,7 +1500,7 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
   const size_t fbytes = (size_t)9 * h->N * h->rsz, tbytes = (size_t)h->N * h->rsz;
   void *sf = nullptr, *sT = nullptr, *ss = nullptr;
   if (cudaMalloc(&sf, fbytes) != cudaSuccess || cudaMalloc(&sT, tbytes) != cudaSuccess ||
-      cudaMalloc(&ss, 2 * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&ss, 4 * sizeof(double)) != cudaSuccess) {
     cudaFree(sf);
     cudaFree(sT);
     cudaFree(ss);
@@ -1472,12 +1512,12 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
   if (rc == PPL_OK) rc = cuda_err(cudaMemcpyAsync(sf, h->f[c0], fbytes, cudaMemcpyDeviceToDevice, h->stream));
   if (rc == PPL_OK) rc = cuda_err(cudaMemcpyAsync(sT, h->T[c0], tbytes, cudaMemcpyDeviceToDevice, h->stream));
   if (rc == PPL_OK)
-    rc = cuda_err(cudaMemcpyAsync(ss, h->stats[c0], 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    rc = cuda_err(cudaMemcpyAsync(ss, h->stats[c0], 4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
 
   auto restore = [&]() -> int {
     CK(cudaMemcpyAsync(h->f[c0], sf, fbytes, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(h->T[c0], sT, tbytes, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->stats[c0], ss, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->stats[c0], ss, 4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     h->cur = c0;
     h->step = step0;
@@ -1485,28 +1525,40 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
     return PPL_OK;
   };
 
-  std::vector<int> cand = {default_rows(h)};
-  for (int H : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-    if (H <= h->ny && std::find(cand.begin(), cand.end(), H) == cand.end()) cand.push_back(H);
-  int best = cand[0];
+  // candidates: each applicable kernel (FP32: two-column and one-column) x rows per CTA
+  std::vector<int> kernels = {PPL_KERNEL_COLUMN};
+  if (pair_applicable(h->cfg)) kernels.insert(kernels.begin(), PPL_KERNEL_PAIR);
+  int best = 0, best_kernel = kernels[0];
   float best_t = -1.0f;
-  for (size_t i = 0; i < cand.size() && rc == PPL_OK; ++i) {
-    rc = apply_rows(h, cand[i]);
-    if (rc == PPL_OK) rc = ppl_step_async(h, 2);  // warm-up (and graph capture below)
-    if (rc == PPL_OK && steps >= kGraphSteps) rc = ppl_step_async(h, kGraphSteps);
-    if (rc == PPL_OK) rc = restore();
-    if (rc == PPL_OK) rc = cuda_err(cudaEventRecord(e0, h->stream));
-    if (rc == PPL_OK) rc = ppl_step_async(h, steps);
-    if (rc == PPL_OK) rc = cuda_err(cudaEventRecord(e1, h->stream));
-    if (rc == PPL_OK) rc = cuda_err(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    if (rc == PPL_OK) rc = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
-    if (rc == PPL_OK) rc = restore();
-    if (rc == PPL_OK && (best_t < 0.0f || ms < best_t)) {
-      best_t = ms;
-      best = cand[i];
+  for (size_t kk = 0; kk < kernels.size() && rc == PPL_OK; ++kk) {
+    const StepVariant v = pick_variant(h->cfg, kernels[kk]);
+    for (int e = 0; e < 2 && rc == PPL_OK; ++e)
+      rc = cuda_err(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+    if (rc != PPL_OK) break;
+    h->var = v;
+    std::vector<int> cand = {default_rows(h)};
+    for (int H : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+      if (H <= h->ny && std::find(cand.begin(), cand.end(), H) == cand.end()) cand.push_back(H);
+    for (size_t i = 0; i < cand.size() && rc == PPL_OK; ++i) {
+      rc = apply_rows(h, cand[i]);
+      if (rc == PPL_OK) rc = ppl_step_async(h, 2);  // warm-up (and graph capture below)
+      if (rc == PPL_OK && steps >= kGraphSteps) rc = ppl_step_async(h, kGraphSteps);
+      if (rc == PPL_OK) rc = restore();
+      if (rc == PPL_OK) rc = cuda_err(cudaEventRecord(e0, h->stream));
+      if (rc == PPL_OK) rc = ppl_step_async(h, steps);
+      if (rc == PPL_OK) rc = cuda_err(cudaEventRecord(e1, h->stream));
+      if (rc == PPL_OK) rc = cuda_err(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      if (rc == PPL_OK) rc = cuda_err(cudaEventElapsedTime(&ms, e0, e1));
+      if (rc == PPL_OK) rc = restore();
+      if (rc == PPL_OK && (best_t < 0.0f || ms < best_t)) {
+        best_t = ms;
+        best = cand[i];
+        best_kernel = kernels[kk];
+      }
     }
   }
+  if (rc == PPL_OK) h->var = pick_variant(h->cfg, best_kernel);
   if (rc == PPL_OK) rc = apply_rows(h, best);
   if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
   cudaFree(sf);
@@ -1563,7 +1615,7 @@ extern "C" {
 
 int ppl_phase_area(ppl_t *h, double rho_lo, double rho_hi, double *area) {
   if (!h || !area || !(rho_hi > rho_lo)) return PPL_E_INVAL;
-  const int nblk = h->stats_blocks;  // partials holds >= 7 * stats_blocks doubles
+  const int nblk = h->stats_blocks;  // partials holds >= kStats * stats_blocks doubles
   const double inv = 1.0 / (rho_hi - rho_lo);
   if (h->prec == PPL_FP64)
     phase_area_partials<double><<<nblk, 256, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], rho_lo, inv,

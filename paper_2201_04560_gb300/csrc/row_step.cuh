@@ -102,6 +102,69 @@ constexpr size_t row_step_smem_bytes() {
   return (size_t)((PF + 3) * 10 + 5 * 4 + 18 + 3) * NT * sizeof(real);
 }
 
+// Deterministic FP64 reduction of sum rho^{n+1} over the grid: the CTA's partial (acc of
+// every thread) is written to its slot; the last CTA to finish sums the slots in a fixed
+// order and publishes rho_bar and the mass for the next step. TANGENT: dacc carries the
+// derivative of the sum as well (two slots per CTA), published as d rho_bar.
+template <int NT, bool TANGENT, typename PT>
+__device__ __forceinline__ void block_mass_finalize(const Params<PT> &P, const StepIO &io, double acc,
+                                                    double dacc) {
+  const int t = threadIdx.x;
+  constexpr int K = TANGENT ? 2 : 1;
+  __shared__ double red[K][NT / 32];
+  __shared__ bool am_last;
+  double v[K];
+  v[0] = acc;
+  if (TANGENT) v[K - 1] = dacc;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    if ((t & 31) == 0) red[j][t >> 5] = v[j];
+  }
+  __syncthreads();
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (t == 0) {
+    for (int j = 0; j < K; ++j) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[j][w];
+      io.partials[(size_t)bid * K + j] = s;
+    }
+    __threadfence();
+    const unsigned done = atomicAdd(io.counter, 1u);
+    am_last = (done == nblk - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double s[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      s[j] = 0.0;
+      for (unsigned b = t; b < nblk; b += NT) s[j] += __ldcg(io.partials + (size_t)b * K + j);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if ((t & 31) == 0) red[j][t >> 5] = s[j];
+    __syncthreads();
+    if (t == 0) {
+      double tot[K];
+      for (int j = 0; j < K; ++j) {
+        tot[j] = 0.0;
+        for (int w = 0; w < NT / 32; ++w) tot[j] += red[j][w];
+      }
+      io.stats_out[0] = tot[0] * P.inv_nodes;
+      io.stats_out[1] = tot[0];
+      if (TANGENT) io.stats_out[2] = tot[K - 1] * P.inv_nodes;
+      *io.counter = 0u;
+    }
+  }
+}
+
 // SIMPLE: every row the CTA touches is an interior row (no wall, outflow or periodic
 // wrap in y), so all row classification folds away at compile time.
 template <typename real, bool ENERGY, int NT, int PF, bool SIMPLE>
@@ -130,7 +193,8 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   const LineMap cm = map_line(gx, P.nx, P.hbc[0], P.hbc[1], 0);
   const bool col_bnd = cm.src == 0 || cm.src == P.nx - 1;  // node may sit on an x boundary line
   const long long plane = P.plane;
-  const real rho_bar = real(io.stats_in[0]);
+  real rho_bar = real(io.stats_in[0]);
+  if constexpr (is_dual<real>::value) rho_bar = Dual(io.stats_in[0], io.stats_in[2]);
   const bool xwall_strip = (P.hbc[0] == WALL && x0 - 3 < 0) || (P.hbc[1] == WALL && x0 + W + 3 > P.nx - 1);
   const bool xout_strip = (P.hbc[0] == OUTFLOW && x0 - 3 <= 0) || (P.hbc[1] == OUTFLOW && x0 + W + 3 >= P.nx - 1);
   const bool any_outflow = P.hbc[0] == OUTFLOW || P.hbc[1] == OUTFLOW || P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
@@ -144,7 +208,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   real *Tout = reinterpret_cast<real *>(io.T_out);
   const int n_it = yb - ya + 6;  // rows ya-3 .. yb+2 pass through S1
   unsigned flags = 0;
-  double acc = 0.0;
+  double acc = 0.0, dacc = 0.0;  // FP64 mass partial (and its tangent)
   real acc_s = real(0), acc_c = real(0);  // FP32 path: compensated per-thread sum
 
   auto row_map = [&](int g) -> LineMap {
@@ -435,6 +499,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
                                                  : (any_outflow ? real(wcol) : real(1));
         if (sizeof(real) != 4) {
           acc += double(wr * rho_new);
+          dacc += tangent_of(wr * rho_new);
         } else {
           // compensated FP32 sum of this thread's column (FP64 beyond the thread)
           const real yk = wr * rho_new - acc_c;
@@ -457,41 +522,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   if (sizeof(real) == 4) acc = double(acc_s) - double(acc_c);
   if (flags) atomicOr(io.status, flags);
 
-  // ---- deterministic FP64 reduction of sum rho^{n+1} ----
-  __shared__ double red[NT / 32];
-  __shared__ bool am_last;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((t & 31) == 0) red[t >> 5] = acc;
-  __syncthreads();
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (t == 0) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
-    io.partials[bid] = s;
-    __threadfence();
-    const unsigned done = atomicAdd(io.counter, 1u);
-    am_last = (done == nblk - 1);
-  }
-  __syncthreads();
-  if (am_last) {
-    __threadfence();
-    double s = 0.0;
-    for (unsigned b = t; b < nblk; b += NT) s += __ldcg(io.partials + b);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __syncthreads();
-    if ((t & 31) == 0) red[t >> 5] = s;
-    __syncthreads();
-    if (t == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < NT / 32; ++w) tot += red[w];
-      io.stats_out[0] = tot * P.inv_nodes;
-      io.stats_out[1] = tot;
-      *io.counter = 0u;
-    }
-  }
+  block_mass_finalize<NT, is_dual<real>::value>(P, io, acc, dacc);
 }
 
 

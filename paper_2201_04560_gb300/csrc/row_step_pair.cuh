@@ -1,0 +1,365 @@
+// FP32 fused step with two columns per thread (packed f32x2 arithmetic) for domains that
+// are periodic in x, hydrodynamically and thermally, with an even nx.
+//
+// The same row-marching pipeline as row_step.cuh (stages S1..S4 at row lags 0..3, rings
+// of per-row quantities in shared memory), with each thread owning the adjacent columns
+// (2t, 2t + 1) of a strip of 2 NT columns: 4 halo columns on each side, 2 NT - 8 interior
+// columns. Both columns of a thread are computed by one packed instruction wherever the
+// arithmetic allows (F2 in lane2.cuh), the staged rows and the stores move 8 bytes per
+// thread, and a column's neighbours come from one 8-byte and two 4-byte shared-memory
+// reads per pair. With x periodic and nx even, a pair never straddles the domain edge
+// and its global address is 8-byte aligned. Rows (walls, outflow, Dirichlet lines in y)
+// are handled exactly as in the one-column kernel; only per-node boundary data of a wall
+// row (rho_w, T_w, the Dirichlet mask) is looked up column by column.
+#pragma once
+
+#include "lane2.cuh"
+#include "row_step.cuh"
+
+namespace ppl_dev {
+
+// values of the columns (2t - 1, 2t), (2t, 2t + 1), (2t + 1, 2t + 2) of one ring row
+struct Trip {
+  F2 l, c, r;
+};
+template <int SW>
+__device__ __forceinline__ Trip trip(const float *row, int t) {
+  const float2 c = *reinterpret_cast<const float2 *>(row + 2 * t);
+  const float l = row[max(2 * t - 1, 0)], r = row[min(2 * t + 2, SW - 1)];
+  return {F2(l, c.x), F2(c), F2(c.y, r)};
+}
+__device__ __forceinline__ F2 ld2(const float *p) { return F2(*reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<float2 *>(p) = v.v; }
+__device__ __forceinline__ void cp_async8(float *smem_dst, const float *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+template <int NT, int PF>
+constexpr size_t row_step_pair_smem_bytes() {
+  return (size_t)((PF + 3) * 10 + 5 * 4 + 18 + 3) * (2 * NT) * sizeof(float);
+}
+
+template <bool ENERGY, int NT, int PF, bool SIMPLE>
+__device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int H,
+                                              unsigned char *smem_raw) {
+  constexpr int D = PF + 3;
+  constexpr int SW = 2 * NT;  // strip columns
+  constexpr int W = SW - 8;   // interior columns
+  float *stg = reinterpret_cast<float *>(smem_raw);  // [D][10][SW]
+  float *rpsi = stg + D * 10 * SW;                    // rings [4][SW], row mod 4
+  float *rrho = rpsi + 4 * SW;
+  float *rT = rrho + 4 * SW;
+  float *rux = rT + 4 * SW;
+  float *ruy = rux + 4 * SW;
+  float *rfs = ruy + 4 * SW;  // [3][6][SW] sideways post-collision populations, row mod 3
+  float *rTs = rfs + 18 * SW;  // [3][SW] first Heun stage, row mod 3
+  const float third = 1.0f / 3.0f, twelfth = 1.0f / 12.0f;
+  const float big = 3.0e38f;
+
+  const int t = threadIdx.x;
+  const int c2 = 2 * t;  // strip column of lane 0
+  const int x0 = blockIdx.x * W;
+  const int ya = blockIdx.y * H;
+  const int yb = min(ya + H, P.ny);
+  const int gx0 = x0 - 4 + c2;  // even
+  int src0 = gx0 % P.nx;
+  if (src0 < 0) src0 += P.nx;
+  const int col0 = src0, col1 = src0 + 1;  // in-domain columns of the two lanes
+  const long long plane = P.plane;
+  const float rho_bar = (float)io.stats_in[0];
+  const bool any_outflow = P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
+  const bool t_s4 = t >= 2 && t < NT - 2 && gx0 < P.nx;  // both lanes interior and in the domain
+  const float *fin = reinterpret_cast<const float *>(io.f_in) + src0;
+  const float *Tin = reinterpret_cast<const float *>(io.T_in) + src0;
+  float *fout = reinterpret_cast<float *>(io.f_out);
+  float *Tout = reinterpret_cast<float *>(io.T_out);
+  const int n_it = yb - ya + 6;
+  unsigned flags = 0;
+  F2 acc_s(0.0f), acc_c(0.0f);  // compensated per-lane mass sums
+
+  auto row_map = [&](int g) -> LineMap {
+    if (SIMPLE) {
+      LineMap m;
+      m.src = g;
+      m.solid = 0;
+      m.wall = -1;
+      m.outflow = 0;
+      return m;
+    }
+    return map_line(g, P.ny, P.hbc[2], P.hbc[3], 2);
+  };
+  auto stage_row = [&](int q, int slot) {
+    const long long k = (long long)row_map(q).src * P.nx;
+    float *dst = stg + slot * 10 * SW + c2;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cp_async8(dst + i * SW, fin + i * plane + k);
+    cp_async8(dst + 9 * SW, Tin + k);
+  };
+  auto lane_ok = [](F2 v) { return v.lo() >= 0.0f && v.hi() >= 0.0f; };
+
+#pragma unroll
+  for (int j = 0; j < PF; ++j) {
+    if (j < n_it) stage_row(ya - 3 + j, j);
+    cp_async_commit();
+  }
+
+  F2 c1jx(0.0f), c1jy(0.0f), n1jx(0.0f), n1jy(0.0f);
+  F2 f0n(0.0f), f2n(0.0f), f4n(0.0f), f0c(0.0f), f2c1(0.0f), f2c2(0.0f);
+  S3Carry<F2> cc2{}, nn2{};
+  S4Carry<F2> cur{}, nxt{};
+  int f3 = 0;
+  for (int iq = 0; iq < n_it; ++iq) {
+    const int q = ya - 3 + iq;
+    if (iq + PF < n_it) stage_row(q + PF, (iq + PF) % D);
+    cp_async_commit();
+    cp_async_wait<PF>();
+    const int s4_0 = iq & 3, s4_1 = (iq + 3) & 3, s4_2 = (iq + 2) & 3, s4_3 = (iq + 1) & 3;
+    const int f_r3 = f3, f_r2 = f3 == 2 ? 0 : f3 + 1, f_r4 = f3 == 0 ? 2 : f3 - 1;
+
+    // ---- S1: row q ----
+    {
+      const LineMap rm = row_map(q);
+      const float *st = stg + (iq % D) * 10 * SW + c2;
+      F2 f[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = ld2(st + i * SW);
+      const F2 Tt = ld2(st + 9 * SW);
+      const F2 delta = ((f[0] + (f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
+      const F2 rho = P.rho_ref + delta;
+      F2 psi(0.0f);
+      if (!rm.solid) {
+        const F2 arg = psi_arg(P, rho, P.T_ref + Tt);
+        if (!lane_ok(arg)) flags |= FLAG_PSI_NEG;
+        psi = sqrt(fmax(arg, F2(0.0f)));
+      }
+      const int i0 = s4_0 * SW + c2;
+      st2(rpsi + i0, psi);
+      st2(rrho + i0, rho);
+      st2(rT + i0, Tt);
+      n1jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+      n1jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    }
+    __syncthreads();
+
+    // ---- S2: row q-1 ----
+    if (iq >= 2) {
+      const int r = q - 1;
+      const LineMap rm = row_map(r);
+      const int i0 = s4_1 * SW, iu = s4_0 * SW, id = s4_2 * SW;
+      if (!rm.solid) {
+        const Trip pu = trip<SW>(rpsi + iu, t), pm = trip<SW>(rpsi + i0, t), pd = trip<SW>(rpsi + id, t);
+        const F2 p1 = pm.r, p3 = pm.l, p2 = pu.c, p4 = pd.c, p5 = pu.r, p6 = pu.l, p7 = pd.l, p8 = pd.r;
+        F2 sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
+        F2 sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
+        const F2 psi_c = pm.c;
+        const F2 dsum = twelfth * (p5 + p6 + p7 + p8 - 4.0f * psi_c);
+        F2 qxx = third * (p1 + p3 - 2.0f * psi_c) + dsum;
+        F2 qyy = third * (p2 + p4 - 2.0f * psi_c) + dsum;
+        const F2 qxy = twelfth * (p5 - p6 + p7 - p8);
+        if (!SIMPLE && rm.wall >= 0) {
+          // solid links of a y wall: see the one-column kernel (Eqs. shanchen-walls,
+          // psi-based-formula, Q-psi-based, mod-psi-based-formula, Q-mod-psi-based)
+          const int ws = rm.wall;
+          F2 pf, pq;
+          if (P.mod_psi) {
+            pf = P.Gw_over_G * psi_c;
+            pq = psi_c;
+          } else {
+            const F2 Tw = P.T_ref + ld2(rT + i0 + c2);
+            const float a0 = psi_arg(P, wall_rho_w(P, ws, col0, rm.src), Tw.lo());
+            const float a1 = psi_arg(P, wall_rho_w(P, ws, col1, rm.src), Tw.hi());
+            if (!(a0 >= 0.0f) || !(a1 >= 0.0f)) flags |= FLAG_PSI_NEG;
+            pf = pq = F2(sqrtf(fmaxf(a0, 0.0f)), sqrtf(fmaxf(a1, 0.0f)));
+          }
+          const F2 hw = 0.5f * pf;
+          if (ws == 2) sy = sy - hw;
+          else sy = sy + hw;
+          qxx = qxx + (1.0f / 6.0f) * pq;
+          qyy = qyy + 0.5f * pq;
+        }
+        const F2 qf = P.kappa_G2 * psi_c;
+        nn2.qxx = qf * qxx;
+        nn2.qyy = qf * qyy;
+        nn2.qxy = qf * qxy;
+        const F2 rho = ld2(rrho + i0 + c2);
+        const F2 gps = (-P.G) * psi_c;
+        const F2 fmx = gps * sx, fmy = gps * sy;
+        const F2 Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
+        const F2 inv_rho = 1.0f / rho;
+        const F2 ux = (c1jx + 0.5f * Fx) * inv_rho;
+        const F2 uy = (c1jy + 0.5f * Fy) * inv_rho;
+        st2(rux + i0 + c2, ux);
+        st2(ruy + i0 + c2, uy);
+        nn2.fmx = fmx;
+        nn2.fmy = fmy;
+        nn2.fm2 = (P.G * P.G) * (sx * sx + sy * sy);
+        nn2.inv_rho = inv_rho;
+        if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
+          st2(rux + s4_3 * SW + c2, ux);
+          st2(ruy + s4_3 * SW + c2, -uy);
+        }
+      } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny
+        st2(rux + i0 + c2, ld2(rux + s4_3 * SW + c2));
+        st2(ruy + i0 + c2, -ld2(ruy + s4_3 * SW + c2));
+      }
+      __syncthreads();
+    }
+
+    // ---- S3: row q-2 ----
+    if (iq >= 4) {
+      const int r = q - 2;
+      const LineMap rm = row_map(r);
+      const int i0 = s4_2 * SW, iu = s4_1 * SW, id = s4_3 * SW;
+      if (!rm.solid) {
+        const float *st = stg + ((iq + D - 2) % D) * 10 * SW + c2;
+        F2 fd[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fd[i] = ld2(st + i * SW);
+        const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
+        const F2 rho = ld2(rrho + i0 + c2);
+        const F2 ux = ld2(rux + i0 + c2), uy = ld2(ruy + i0 + c2);
+        const F2 Fx = cc2.fmx + P.gx * (rho - rho_bar), Fy = cc2.fmy + P.gy * (rho - rho_bar);
+        F2 s_eta(P.s[7]);
+        if (P.var_eta) s_eta = 1.0f / (3.0f * (P.eta_v + (P.eta_l - P.eta_v) * ((rho - P.rho_v) * P.inv_drho)) + 0.5f);
+        collide(P, fd, rho, delta, ux, uy, Fx, Fy, cc2.fm2, cc2.qxx, cc2.qyy, cc2.qxy, s_eta);
+        float *fs = rfs + f_r2 * 6 * SW + c2;
+        st2(fs + 0 * SW, fd[1]);
+        st2(fs + 1 * SW, fd[3]);
+        st2(fs + 2 * SW, fd[5]);
+        st2(fs + 3 * SW, fd[6]);
+        st2(fs + 4 * SW, fd[7]);
+        st2(fs + 5 * SW, fd[8]);
+        f0n = fd[0];
+        f2n = fd[2];
+        f4n = fd[4];
+        nxt.Fx = Fx;
+        nxt.Fy = Fy;
+        if (ENERGY) {
+          const F2 T0 = ld2(rT + i0 + c2);
+          nxt.ux = ux;
+          nxt.uy = uy;
+          dpdT_parts(P, rho, &nxt.A, &nxt.B);
+          nxt.inv_rcv = cc2.inv_rho * P.cv_inv;
+          nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
+          const Trip ru = trip<SW>(rrho + iu, t), rmd = trip<SW>(rrho + i0, t), rd = trip<SW>(rrho + id, t);
+          nxt.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l - rd.l + rd.r));
+          nxt.gdy = P.dlam * (third * (ru.c - rd.c) + twelfth * (ru.r + ru.l - rd.l - rd.r));
+          const Trip xu = trip<SW>(rux + iu, t), xm = trip<SW>(rux + i0, t), xd = trip<SW>(rux + id, t);
+          const Trip yu = trip<SW>(ruy + iu, t), yd = trip<SW>(ruy + id, t);
+          nxt.div = third * (xm.r - xm.l) + twelfth * (xu.r - xu.l - xd.l + xd.r) + third * (yu.c - yd.c) +
+                    twelfth * (yu.r + yu.l - yd.l - yd.r);
+          F2 Ts;
+          if (!SIMPLE && rm.outflow) {
+            Ts = ld2(rTs + f_r3 * SW + c2);  // outflow row: copy of the first interior row
+            nxt.k1 = F2(0.0f);
+          } else {
+            const Trip tu = trip<SW>(rT + iu, t), tm = trip<SW>(rT + i0, t), td = trip<SW>(rT + id, t);
+            const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
+            const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
+            const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * T0) +
+                           (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * T0);
+            const F2 k1 = -(ux * gtx + uy * gty) + (nxt.lam * lap + nxt.gdx * gtx + nxt.gdy * gty) * nxt.inv_rcv -
+                          T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0) * nxt.div * nxt.inv_rcv;
+            nxt.k1 = k1;
+            Ts = T0 + k1;
+            if (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) {  // Dirichlet nodes of a y line
+              float tw0, tw1;
+              const bool d0 = t_fixed(P, col0, rm.src, &tw0), d1 = t_fixed(P, col1, rm.src, &tw1);
+              if (d0 || d1) {
+                Ts = F2(d0 ? tw0 - P.T_ref : Ts.lo(), d1 ? tw1 - P.T_ref : Ts.hi());
+                nxt.k1 = F2(d0 ? 0.0f : k1.lo(), d1 ? 0.0f : k1.hi());
+              }
+            }
+          }
+          st2(rTs + f_r2 * SW + c2, Ts);
+          if (!SIMPLE && r == 1 && P.hbc[2] == WALL) st2(rTs + f_r4 * SW + c2, Ts);  // mirror ghost of row -1
+        }
+      } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {
+        st2(rTs + f_r2 * SW + c2, ld2(rTs + f_r4 * SW + c2));  // mirror ghost of row ny
+      }
+      __syncthreads();
+    }
+
+    // ---- S4: row q-3 ----
+    if (iq >= 6 && t_s4) {
+      const int r = q - 3;
+      const LineMap rm = row_map(r);
+      if (!rm.outflow) {
+        // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi)
+        const float *lo = rfs + f_r4 * 6 * SW, *mid = rfs + f_r3 * 6 * SW, *hi = rfs + f_r2 * 6 * SW;
+        F2 fd[9];
+        fd[0] = f0c;
+        fd[1] = trip<SW>(mid + 0 * SW, t).l;
+        fd[2] = f2c2;
+        fd[3] = trip<SW>(mid + 1 * SW, t).r;
+        fd[4] = f4n;
+        fd[5] = trip<SW>(lo + 2 * SW, t).l;
+        fd[6] = trip<SW>(lo + 3 * SW, t).r;
+        fd[7] = trip<SW>(hi + 4 * SW, t).r;
+        fd[8] = trip<SW>(hi + 5 * SW, t).l;
+        if (!SIMPLE && rm.wall >= 0) zou_he<F2>(rm.wall, fd, ev(-0.5f * cur.Fx), ev(-0.5f * cur.Fy));
+        const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
+        const F2 rho_new = P.rho_ref + delta;
+        const F2 T_old = ld2(rT + s4_3 * SW + c2);
+        F2 T_new = T_old;
+        if (ENERGY) {
+          const Trip tm = trip<SW>(rTs + f_r3 * SW, t), tu = trip<SW>(rTs + f_r2 * SW, t),
+                     td = trip<SW>(rTs + f_r4 * SW, t);
+          const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
+          const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
+          const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * tm.c) +
+                         (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * tm.c);
+          const F2 k2 = -(cur.ux * gtx + cur.uy * gty) + (cur.lam * lap + cur.gdx * gtx + cur.gdy * gty) * cur.inv_rcv -
+                        T_dpdT(P, cur.A, cur.B, P.T_ref + tm.c) * cur.div * cur.inv_rcv;
+          T_new = T_new + 0.5f * (cur.k1 + k2);
+          if (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) {  // Dirichlet nodes keep their value
+            float tw;
+            const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
+            T_new = F2(d0 ? T_old.lo() : T_new.lo(), d1 ? T_old.hi() : T_new.hi());
+          }
+        }
+        const long long k = (long long)r * P.nx + gx0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st2(fout + i * plane + k, fd[i]);
+        st2(Tout + k, T_new);
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const float rn = l ? rho_new.hi() : rho_new.lo(), tn = l ? T_new.hi() : T_new.lo();
+          if (!(rn > 0.0f && rn <= big && fabsf(tn) <= big))
+            flags |= (rn == rn && fabsf(tn) <= big && rn <= big) ? FLAG_RHO_NONPOS : FLAG_NAN;
+        }
+        const float wr = (!SIMPLE && any_outflow) ? (float)line_weight(r, P.ny, P.hbc[2], P.hbc[3]) : 1.0f;
+        const F2 yk = wr * rho_new - acc_c;
+        const F2 tk = acc_s + yk;
+        acc_c = (tk - acc_s) - yk;
+        acc_s = tk;
+      }
+    }
+    c1jx = n1jx;
+    c1jy = n1jy;
+    cc2 = nn2;
+    cur = nxt;
+    f0c = f0n;
+    f2c2 = f2c1;
+    f2c1 = f2n;
+    f3 = f3 == 2 ? 0 : f3 + 1;
+  }
+  cp_async_wait<0>();
+  double acc = ((double)acc_s.lo() - (double)acc_c.lo()) + ((double)acc_s.hi() - (double)acc_c.hi());
+  if (flags) atomicOr(io.status, flags);
+  block_mass_finalize<NT, false>(P, io, acc, 0.0);
+}
+
+template <bool ENERGY, int NT, int PF>
+__global__ void __launch_bounds__(NT, 320 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ya = blockIdx.y * H;
+  const int yb = min(ya + H, P.ny);
+  if (ya - 3 >= 1 && yb + 2 <= P.ny - 2)
+    row_body_pair<ENERGY, NT, PF, true>(P, io, H, smem_raw);
+  else
+    row_body_pair<ENERGY, NT, PF, false>(P, io, H, smem_raw);
+}
+
+}  // namespace ppl_dev

@@ -12,6 +12,7 @@ static const void *fp64_fn() {
 StepVariant step_variant_fp64() {
   StepVariant v;
   v.nt = kNT64;
+  v.width = kNT64 - 6;
   v.smem = row_step_smem_bytes<kNT64, kPF64, double>();
   v.fn[0] = fp64_fn<false>();
   v.fn[1] = fp64_fn<true>();

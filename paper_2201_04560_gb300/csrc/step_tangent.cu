@@ -13,6 +13,7 @@ static const void *tangent_fn() {
 StepVariant step_variant_tangent() {
   StepVariant v;
   v.nt = kNTD;
+  v.width = kNTD - 6;
   v.smem = row_step_smem_bytes<kNTD, kPFD, Dual>();
   v.fn[0] = tangent_fn<false>();
   v.fn[1] = tangent_fn<true>();

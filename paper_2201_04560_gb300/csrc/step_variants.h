@@ -11,14 +11,18 @@ constexpr int kNT64 = 128;
 constexpr int kPF64 = 1;
 constexpr int kNTD = 128;  // tangent (Dual) step
 constexpr int kPFD = 1;
+constexpr int kNTP = 64;   // FP32 two-column kernel: threads per CTA (2 kNTP columns)
+constexpr int kPFP = 1;
 
 struct StepVariant {
-  int nt;        // threads per CTA = strip width incl. halo
+  int nt;        // threads per CTA
+  int width;     // interior columns per CTA (strip width minus the halo)
   size_t smem;   // dynamic shared memory per CTA
   const void *fn[2];  // [energy on]
 };
 
 StepVariant step_variant_fp32();
+StepVariant step_variant_fp32_pair();  // two columns per thread: x periodic (hydro and T), nx even
 StepVariant step_variant_fp64();
 StepVariant step_variant_tangent();  // FP64 value + derivative (Dual)
 

@@ -124,6 +124,10 @@ def load_library(build_if_missing: bool = True):
     L.ppl_set_launch.argtypes = [H, ctypes.c_int32]
     L.ppl_get_launch.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     L.ppl_autotune.argtypes = [H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _PD]
+    L.ppl_select_kernel.argtypes = [H, ctypes.c_int]
+    L.ppl_select_kernel.restype = ctypes.c_int
+    L.ppl_get_kernel.argtypes = [H]
+    L.ppl_get_kernel.restype = ctypes.c_int
     L.ppl_phase_area.argtypes = [H, _D, _D, _PD]
     L.ppl_relative_change.argtypes = [_PD, _PD, ctypes.c_int64, _PD]
     L.ppl_wall_heat_flux.argtypes = [H, ctypes.c_int, _PD]
@@ -343,6 +347,17 @@ class Simulation:
     def set_launch(self, rows_per_cta: int = 0):
         """Rows per CTA of the step kernel (0 = default shape)."""
         _check(self.lib.ppl_set_launch(self.h, int(rows_per_cta)), "ppl_set_launch")
+
+    KERNELS = {"auto": 0, "column": 1, "pair": 2}
+
+    def select_kernel(self, kind: str = "auto"):
+        """FP32 step kernel: "column" (one column per thread), "pair" (two columns per thread,
+        packed f32x2; x-periodic domains with even nx) or "auto"."""
+        _check(self.lib.ppl_select_kernel(self.h, self.KERNELS[kind]), "ppl_select_kernel")
+
+    @property
+    def kernel(self) -> str:
+        return {1: "column", 2: "pair"}[int(self.lib.ppl_get_kernel(self.h))]
 
     def launch(self):
         """(rows per CTA, CTAs per step launch)."""

@@ -204,3 +204,56 @@ def test_sessile_droplet_contact_models_fp64(sim_cls, th, model, axis):
         cfg, ic = _transpose_case(cfg, ic)
     got, want = run_pair(sim_cls, cfg, ic, 400)
     assert_fp64_parity(got, want)
+
+
+@pytest.mark.parametrize("case", ["pool", "droplet", "ragged"])
+def test_pair_kernel_fp32_against_oracle_and_column_kernel(sim_cls, th, case):
+    # the two-column FP32 kernel (packed f32x2) is chosen automatically for x-periodic
+    # domains with even nx; it meets the FP32 budget against the FP64 oracle and agrees
+    # with the one-column FP32 kernel to FP32 rounding
+    e = th["e"]
+    if case == "pool":
+        rv, rl, _ = th[0.86]
+        cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=250, ny=77, g=3e-5, precision="fp32")
+        steps = 300
+    elif case == "droplet":
+        rv, rl, _ = th[0.8]
+        cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=64, R0=16.0, precision="fp32", kappa=0.3)
+        steps = 400
+    else:
+        rv, rl, _ = th[0.8]
+        cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=246, ny=45, R0=14.0, precision="fp32")
+        cfg.update(gx=2e-5, gy=-4e-5, eta_l=0.1, eta_v=0.05, energy_on=1, lambda_l=0.2, lambda_v=0.2,
+                   s=[1.0, 0.8, 0.9, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25])
+        steps = 200
+    pair = sim_cls(cfg, *ic)
+    assert pair.kernel == "pair"
+    pair.step(steps)
+    got = pair.fields()
+    col = sim_cls(cfg, *ic)
+    col.select_kernel("column")
+    assert col.kernel == "column"
+    col.step(steps)
+    ref = col.fields()
+    for s in (pair, col):
+        s.close()
+    want = oracle.Oracle(dict(cfg, precision="fp64"), *ic)
+    want.step(steps)
+    w = want.fields()
+    for k in ("rho", "T"):
+        assert l1rel(got[k], w[k]) <= 1e-4
+        np.testing.assert_allclose(got[k], ref[k], rtol=2e-5, atol=2e-5 * np.abs(ref[k]).max())
+    np.testing.assert_allclose(got["ux"], ref["ux"], rtol=0, atol=1e-5)
+
+
+def test_pair_kernel_selection_rules(sim_cls, th):
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=63, ny=40, R0=10.0, precision="fp32")
+    with sim_cls(cfg, *ic) as s:
+        assert s.kernel == "column"  # odd nx
+        with pytest.raises(Exception):
+            s.select_kernel("pair")
+    cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=40, R0=10.0, precision="fp64")
+    with sim_cls(cfg, *ic) as s:
+        assert s.kernel == "column"  # FP64

@@ -60,17 +60,25 @@ def rel_inf(a, b):
 @pytest.mark.parametrize("param", ["sigma", "kappa"])
 def test_tangent_matches_central_differences(ppl, th, name, param):
     cfg, ic, steps = make_case(th, name)
+    # central differences with h = 1e-4 carry an O(h^2) truncation error (up to ~2e-5 of
+    # the derivative in the pool case); their Richardson extrapolation with h / 2 removes
+    # it, and the tangent must agree with that to 1e-6
     tan = run(ppl, cfg, ic, steps, precision="fp64_d" + param)
     h = 1e-4
     p0 = cfg[param]
-    plus = run(ppl, cfg, ic, steps, **{param: p0 + h})
-    minus = run(ppl, cfg, ic, steps, **{param: p0 - h})
+    D = {}
+    for hh in (h, h / 2):
+        plus = run(ppl, cfg, ic, steps, **{param: p0 + hh})
+        minus = run(ppl, cfg, ic, steps, **{param: p0 - hh})
+        D[hh] = {f: (plus[f] - minus[f]) / (2 * hh) for f in ("rho", "T", "ux", "uy")}
     for f in ("rho", "T", "ux", "uy"):
-        fd = (plus[f] - minus[f]) / (2 * h)
+        fd = D[h][f]
         if np.max(np.abs(fd)) < 1e-9 and f != "rho":
             assert np.max(np.abs(tan["d"][f])) < 1e-8  # e.g. T frozen in the isothermal phase
             continue
-        assert rel_inf(tan["d"][f], fd) <= 1e-5, (f, rel_inf(tan["d"][f], fd))
+        assert rel_inf(tan["d"][f], fd) <= 1e-4, (f, rel_inf(tan["d"][f], fd))
+        rich = (4 * D[h / 2][f] - D[h][f]) / 3
+        assert rel_inf(tan["d"][f], rich) <= 1e-6, (f, rel_inf(tan["d"][f], rich))
     assert np.max(np.abs(tan["d"]["rho"])) > 1e-6  # the parameter does act on the state
 
 
