@@ -236,6 +236,8 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
     ap.add_argument("--nx", type=int, default=NX, help="grid width (profiling runs; the bench workload is 2048)")
     ap.add_argument("--ny", type=int, default=NY, help="grid height (profiling runs; the bench workload is 4096)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "column", "pair"],
+                    help="FP32 step kernel (profiling runs; auto picks the two-column kernel where it applies)")
     ap.add_argument("--experiment", default=None, choices=sorted(EXPERIMENTS),
                     help="run one of the paper's mesh-refinement studies instead of the throughput step")
     ap.add_argument("--coarse-steps", type=int, default=0, help="experiment length in first-mesh steps")
@@ -280,6 +282,8 @@ def main():
         steps = args.steps if prec == "fp32" else (args.fp64_steps or max(8, args.steps // 8))
         cfg, ic = workload(prec, nx=nx, ny=ny)
         sim = Simulation(cfg, *ic)
+        if prec == "fp32" and args.kernel != "auto":
+            sim.select_kernel(args.kernel)
         sampler = ClockSampler(local) if prec == "fp32" else None
         barrier()
         torch.cuda.synchronize()
