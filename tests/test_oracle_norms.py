@@ -162,3 +162,13 @@ def test_contact_angle_with_a_depleted_wall_layer():
     assert norms.contact_angle(0.38 + 3.06 * (1 + np.tanh(2 * (20 - d) / W)), 3.44) == 180.0
     film = np.where(y < 10, 6.5, 0.38)
     assert np.isnan(norms.contact_angle(film, 3.44))
+
+
+@pytest.mark.slow
+def test_workload_wall_density_gives_a_60_degree_angle():
+    # the pool workload's wall density (written by oracle.contact_calibration) reproduces
+    # its angle in the oracle, and the angle falls as rho_w rises
+    import workloads as W
+    from oracle import contact_calibration as C
+    assert C.static_angle(W.RHO_W_60DEG) == pytest.approx(60.0, abs=1.0)
+    assert C.static_angle(2.3) > 80.0

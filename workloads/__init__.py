@@ -31,6 +31,11 @@ PERIODIC, WALL, OUTFLOW = 0, 1, 2
 T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
 CONTACT_PSI, CONTACT_MOD_PSI = 0, 1  # Eqs. (psi-based-formula), (mod-psi-based-formula)
 
+# psi-based wall density of a 60 degree static contact angle at 0.86 T_c: written by
+# `python -m oracle.contact_calibration 60` (FP64 oracle, 80^2 sessile drop, 12,000 steps,
+# bisection on rho_w; 60.1 deg at 3.35)
+RHO_W_60DEG = 3.35
+
 # rates of the droplet/Stefan/pool runs (Sec. 4.2 and 4.3 of the paper): rho, e, zeta, j, q, j, q, eta, eta
 RATES_STEFAN_POOL = [1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25]
 
@@ -131,11 +136,12 @@ def droplet_vaporization(Tc, rho_v, rho_l, sigma, nx=256, ny=256, R0=40.0, width
 
 def pool_boiling(Tc, rho_v, rho_l, sigma, nx=1024, ny=2048, g=3e-5, g_ref_height=160, T_ratio=0.86,
                  heater_frac=0.2,
-                 dTh_ratio=0.1, rho_w_heater=3.44, rho_w_bottom=6.50, rho_w_top=0.38,
+                 dTh_ratio=0.1, rho_w_heater=RHO_W_60DEG, rho_w_bottom=RHO_W_60DEG, rho_w_top=0.38,
                  pool_frac=2.0 / 3.0, noise_ratio=1e-3, seed=20220112, width=3.0, precision="fp64"):
     """2-D pool boiling (Sec. 4.3): x periodic, Zou-He walls at y = 0 and y = ny-1,
     bottom-centre heater strip of heater_frac * nx nodes held at T_sat + dTh (Dirichlet),
-    adiabatic elsewhere; psi-based wall densities per wall node; liquid pool below
+    adiabatic elsewhere; psi-based wall densities per wall node (a 60 degree contact angle on
+    the bottom wall and the heater, hydrophobic top); liquid pool below
     pool_frac * ny at T_sat with seeded uniform noise of +-noise_ratio * Tc.
 
     Gravity: g is the acceleration of a pool g_ref_height nodes tall (the paper's 160^2
