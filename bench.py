@@ -199,6 +199,10 @@ EXPERIMENTS = {
     "gw-search": ("G_w_search", dict()),
     # pool boiling, rho_wh = 3.44 and T_h = 1.2 T_c: d^N, D^N, Q(t), time shifts
     "pool-refinement": ("pool_boiling_study", dict()),
+    # the batched refinement sequence against stepping its handles one after another
+    "batch-throughput": ("batch_throughput", dict()),
+    # the FP32 path against the FP64 path, per field, on the four synthetic cases
+    "fp32-error": ("fp32_error_study", dict()),
     # sigma and kappa of the 192^2 mesh tuned on the lattice with sensitivity runs (Sec. 3.2)
     "calibration": ("calibration.calibrate_mesh", dict(n_base=128, n=192)),
 }
@@ -211,9 +215,9 @@ def run_experiment(args):
     mod, _, fname = fn.rpartition(".")
     study = getattr(importlib.import_module("paper_2201_04560_gb300." + (mod or "refinement")), fname)
     kw = dict(kw)
-    if args.coarse_steps:
+    if args.coarse_steps and fname not in ("fp32_error_study", "batch_throughput"):
         kw["coarse_steps"] = args.coarse_steps
-    if args.precision in ("fp32", "fp64") and not mod and fname != "G_w_search":
+    if args.precision in ("fp32", "fp64") and not mod and fname not in ("G_w_search", "fp32_error_study"):
         kw["precision"] = args.precision
     t0 = time.time()
     if name == "contact-psi":

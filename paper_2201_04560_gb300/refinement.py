@@ -284,3 +284,125 @@ def pool_boiling_study(meshes=(160, 240, 360, 540), rho_wh=3.44, Th_ratio=1.2, c
     Q = [[q * (n / base_n) ** 3 for q in series] for series, n in zip(Q, meshes)]
     return {"meshes": list(meshes), "substeps": subs, "launch_rows": shapes, "t": t, "d": d, "D": D, "Q": Q,
             "shifts": shifts, "seconds": wall, "rho_wh": rho_wh, "Th_ratio": Th_ratio}
+
+
+def fp32_error_study(steps_scale=1.0):
+    """The FP32 path (FP32 arithmetic, f - w rho_ref and T - T_ref stored in FP32) against the
+    FP64 path (which matches the FP64 oracle to 1e-10) on the synthetic cases shaped like the
+    paper's: per field, the relative L1 difference sum|a - b| / sum|b| (the form of Eq.
+    rel-diff-timestep) and the pointwise maximum relative difference of rho and T, the bulk
+    (coexistence) densities, the droplet radius R(t) of Sec. 4.1 and the Stefan interface
+    position of Sec. 4.2 (where the y-mean density crosses rho_mid)."""
+    out = {}
+    Tc = ppl.tc(EOS["a"], EOS["b"], EOS["R"])
+
+    def pair(cfg, ic, steps, probe=None, every=None):
+        res = {}
+        for prec in ("fp64", "fp32"):
+            with ppl.Simulation(dict(cfg, precision=prec), *ic) as s:
+                series = []
+                done = 0
+                while done < steps:
+                    k = min(every or steps, steps - done)
+                    s.step(k)
+                    done += k
+                    if probe:
+                        series.append(probe(s))
+                res[prec] = (s.fields(), series)
+        return res
+
+    def compare(res, extra=None):
+        a, b = res["fp32"][0], res["fp64"][0]
+        r = {}
+        for f in ("rho", "T"):
+            r[f + "_l1rel"] = float(np.abs(a[f] - b[f]).sum() / np.abs(b[f]).sum())
+            r[f + "_maxrel"] = float(np.max(np.abs(a[f] - b[f]) / np.abs(b[f])))
+        r["rho_min_rel"] = float(abs(a["rho"].min() - b["rho"].min()) / b["rho"].min())
+        r["rho_max_rel"] = float(abs(a["rho"].max() - b["rho"].max()) / b["rho"].max())
+        if extra:
+            r.update(extra(res))
+        return r
+
+    n = lambda x: max(1, int(round(x * steps_scale)))
+    # static droplet (64^2, 0.8 T_c, 5,000 steps)
+    _, rv, rl = coexistence(0.8)
+    cfg, ic = W.static_droplet(Tc, rv, rl, nx=64, ny=64, R0=16.0)
+    out["static_droplet_64"] = compare(pair(cfg, ic, n(5000)))
+    # Stefan strip (1024 x 4, 0.86 T_c + 0.05 T_c wall), interface position
+    Tc_, rv, rl = coexistence(0.86)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], 0.86 * Tc)
+    cfg, ic = W.stefan_strip(Tc, rv, rl, sigma, nx=1024, ny=4, n_vapour=10)
+    mid = 0.5 * (rv + rl)
+
+    def front(s):
+        prof = s.fields()["rho"].mean(axis=0)
+        i = int(np.argmax(prof > mid))
+        return float(i - 1 + (mid - prof[i - 1]) / (prof[i] - prof[i - 1])) if i > 0 else float("nan")
+
+    def front_err(res):
+        a, b = np.array(res["fp32"][1]), np.array(res["fp64"][1])
+        return {"front_max_abs_nodes": float(np.nanmax(np.abs(a - b))), "front_final": float(b[-1])}
+
+    out["stefan_1024x4"] = compare(pair(cfg, ic, n(20000), front, n(2000)), front_err)
+    # droplet vaporization (256^2, 0.8 / 0.9 T_c, kappa 0.3), radius R(t)
+    _, rv, rl = coexistence(0.8)
+    cfg, ic = W.droplet_vaporization(Tc, rv, rl, ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"],
+                                                             0.8 * Tc), nx=256, ny=256, R0=40.0, iso_steps=n(2000))
+    midv, band = 0.5 * (rv + rl), 0.05 * (rl - rv)
+    radius = lambda s: math.sqrt(s.phase_area(midv - band, midv + band) / math.pi)
+
+    def radius_err(res):
+        a, b = np.array(res["fp32"][1]), np.array(res["fp64"][1])
+        return {"radius_max_rel": float(np.max(np.abs(a - b) / b)), "radius_final": float(b[-1])}
+
+    out["droplet_vaporization_256"] = compare(pair(cfg, ic, n(20000), radius, n(1000)), radius_err)
+    # pool boiling (1024 x 2048)
+    _, rv, rl = coexistence(0.86)
+    cfg, ic = W.pool_boiling(Tc, rv, rl, sigma, nx=1024, ny=2048)
+    out["pool_boiling_1024x2048"] = compare(pair(cfg, ic, n(2000)))
+    return out
+
+
+def batch_throughput(meshes=(128, 256, 512), outer=200, precision="fp32", autotune_steps=64):
+    """The batched refinement sequence (concurrent graph branches) against stepping the same
+    handles one after another: wall time of `outer` outer steps (1 : 4 : 16 steps per coarse
+    step for 128^2 / 256^2 / 512^2) each way, from the same initial states."""
+    base_n = meshes[0]
+    Tc, rv, rl = coexistence(0.8)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], 0.8 * Tc)
+    base, _ = W.droplet_vaporization(Tc, rv, rl, sigma, nx=base_n, ny=base_n, R0=base_n * 0.15,
+                                     iso_steps=10 * outer, precision=precision)
+    subs = substeps(meshes, base_n)
+
+    def make():
+        sims = []
+        for n in meshes:
+            c, Tcn = _refined(base, base_n, n, 0.8)
+            _, ic = W.droplet_vaporization(Tcn, rv, rl, c["sigma"], nx=n, ny=n, R0=n * 0.15, width=3.0 * n / base_n,
+                                           iso_steps=c["iso_steps"], precision=precision)
+            s = ppl.Simulation(c, *ic)
+            if autotune_steps:
+                s.autotune(autotune_steps)
+            sims.append(s)
+        return sims
+
+    sims = make()
+    for s, k in zip(sims, subs):  # warm-up (graph capture)
+        s.step(2 * k)
+    t0 = time.perf_counter()
+    for s, k in zip(sims, subs):
+        s.step(outer * k)
+    seq = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    sims = make()
+    with ppl.Batch(sims, subs) as b:
+        b.step(2)
+        t0 = time.perf_counter()
+        b.step(outer)
+        bat = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    nodes = sum(n * n * k for n, k in zip(meshes, subs)) * outer
+    return {"meshes": list(meshes), "substeps": subs, "outer": outer, "sequential_s": seq, "batch_s": bat,
+            "speedup": seq / bat, "batch_mlups": nodes / bat / 1e6, "sequential_mlups": nodes / seq / 1e6}
