@@ -14,13 +14,14 @@ LIB = os.path.join(BUILD, "libppl.so")
 # square root (its error is budgeted against the FP64 oracle), the FP64 step is IEEE
 UNITS = {
     "ppl.cu": [],
+    "tools.cu": [],
     "thermo.cu": [],
     "step_fp64.cu": [],
     "step_fp32.cu": ["--use_fast_math"],
     "step_tangent.cu": [],
 }
 SOURCES = [os.path.join(CSRC, u) for u in UNITS]
-DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "dual.cuh", "row_step.cuh", "step_variants.h")] + [
+DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "dual.cuh", "lane2.cuh", "row_step.cuh", "row_step_pair.cuh", "sim.cuh", "step_variants.h")] + [
     os.path.join(ROOT, "include", "ppl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
