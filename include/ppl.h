@@ -218,9 +218,10 @@ void ppl_destroy(ppl_t *h);
  *
  * Scratch: the FP64 per-CTA partials of the mass reduction and a completion counter live
  * in a static device array of the library (4096 partials, 32 KB), held by every GPU that
- * loads the library until the process exits. A grid that needs more than 4096 CTAs
- * (about nx > 4096 * 122 columns, or more rows per column strip than one wave of CTAs
- * covers) is rejected with PPL_E_INVAL before anything runs. The first call on each device
+ * loads the library until the process exits. A launch grid of more than 4096 CTAs (the
+ * default shape is one wave of resident CTAs, so only very wide grids, beyond about 4096
+ * column strips of 120-122 columns, reach it) is rejected with PPL_E_INVAL before anything
+ * runs. The sensitivity precisions (PPL_FP64_DSIGMA/DKAPPA) are rejected as well. The first call on each device
  * resolves the scratch's device address and sets kernel attributes; make that first call
  * before any stream capture. All calls share the one scratch array and it keeps the last
  * call's contents (the counter is cleared by each call): calls that overlap on the GPU,
