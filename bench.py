@@ -60,7 +60,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -154,7 +154,10 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle
-    nx, ny = 512, 1024
+    # the crop shrinks with the step count so that the whole run stays near 80 s of CPU
+    # (the oracle updates about 2.5 M nodes/s on one core)
+    nodes = max(256 * 32, int(2.0e8 / (args.steps + args.warmup)))
+    nx, ny = 256, max(32, min(NY, nodes // 256))
     cfg, ic = workload("fp64", nx=nx, ny=ny, thermo="oracle")
     o = oracle.Oracle(cfg, *ic)
     o.step(args.warmup)
@@ -251,7 +254,7 @@ def run_experiment(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=0, help="FP64 timed steps (default steps/8, >= 8)")
