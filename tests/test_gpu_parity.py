@@ -257,3 +257,38 @@ def test_pair_kernel_selection_rules(sim_cls, th):
     cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=40, R0=10.0, precision="fp64")
     with sim_cls(cfg, *ic) as s:
         assert s.kernel == "column"  # FP64
+
+
+@pytest.mark.parametrize("case", ["stefan_y", "sessile_psi", "sessile_mod"])
+def test_pair_kernel_wall_rows_fp32(sim_cls, th, case):
+    # the two-column kernel's row-boundary paths: a psi-based wall row held at a Dirichlet
+    # temperature with an outflow row opposite (the Stefan strip turned to run along y),
+    # and both contact models on y walls, against the oracle and the one-column kernel
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    if case == "stefan_y":
+        cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=8, n_vapour=10, precision="fp32")
+        cfg, ic = _transpose_case(cfg, ic)
+        steps = 1500
+    else:
+        cm = W.CONTACT_PSI if case == "sessile_psi" else W.CONTACT_MOD_PSI
+        cfg, ic = W.sessile_droplet(e.Tc, rv, rl, th["sigma086"], nx=70, ny=41, R0=13.0, contact_model=cm,
+                                    rho_w=4.0, G_w=-0.8, precision="fp32")
+        cfg.update(kappa=0.3)
+        steps = 600
+    pair = sim_cls(cfg, *ic)
+    assert pair.kernel == "pair"
+    pair.step(steps)
+    got = pair.fields()
+    pair.close()
+    col = sim_cls(cfg, *ic)
+    col.select_kernel("column")
+    col.step(steps)
+    ref = col.fields()
+    col.close()
+    want = oracle.Oracle(dict(cfg, precision="fp64"), *ic)
+    want.step(steps)
+    w = want.fields()
+    for k in ("rho", "T"):
+        assert l1rel(got[k], w[k]) <= 1e-4
+        np.testing.assert_allclose(got[k], ref[k], rtol=5e-5, atol=5e-5 * np.abs(ref[k]).max())
