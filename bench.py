@@ -96,19 +96,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_traffic():
-    """ncu DRAM bytes of one FP32 step launch at the bench size, if taken on the current kernel sources."""
+def profile_record(name, key):
+    """A figure from a committed ncu summary (profiles/<name>), if it was taken on the current
+    kernel sources (their sha256 is recorded beside it), else None."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
             rec = json.load(fh)
         h = hashlib.sha256()
         for f in rec["sources"]:
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
-        return rec["traffic_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+        return rec[key] if h.hexdigest() == rec["sources_sha256"] else None
     except (OSError, KeyError, ValueError):
         return None
+
+
+def kernel_traffic():
+    """ncu DRAM bytes of one FP32 step launch at the bench size, if taken on the current kernel sources."""
+    return profile_record("traffic.json", "traffic_bytes_per_launch")
+
+
+# GB300's dense FP64 rate is 1.25 TFLOP/s nominal: 2 FP64 FMA thread-operations per SM per clock
+# (152 SMs x 2.07 GHz x 2 x 2 flops); the FP64 step's roofline is its FP64-pipe instruction rate
+FP64_OPS_PER_SM_CLOCK = 2.0
 
 
 def measured_peaks():
@@ -146,6 +157,19 @@ def cpu_oracle_sample(steps=3):
     dt = time.perf_counter() - t0
     return {"value": NX * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": "%dx%d pool boiling, %d FP64 steps, single-threaded C oracle" % (NX, NY, steps)}
+
+
+def fp64_roofline(mlups64, ach_gbs, hbm, peaks, torch):
+    """FP64 step against GB300's FP64 pipe: FP64-pipe thread-instructions per node (ncu,
+    profiles/fp64_pipe.json) x node updates per second, over 2 per SM per clock."""
+    per_node = profile_record("fp64_pipe.json", "fp64_pipe_thread_inst_per_node")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = FP64_OPS_PER_SM_CLOCK * sms * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = per_node * mlups64 * 1e6 if per_node else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP64 thread-instr/s",
+            "frac": achieved / peak if achieved else None,
+            "peak_kind": "nominal 1.25 TFLOP/s dense FP64 = 2 FMA per SM per clock at the max SM clock",
+            "achieved_gbs": ach_gbs, "hbm_frac": ach_gbs / hbm, "bytes_per_node": BYTES_PER_NODE["fp64"]}
 
 
 def run_reference(args):
@@ -369,8 +393,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                      "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,
-                 "roofline": {"bound": "alu", "achieved_gbs": ach64, "hbm_frac": ach64 / hbm,
-                              "bytes_per_node": BYTES_PER_NODE["fp64"]}},
+                 "roofline": fp64_roofline(mlups64, ach64, hbm, peaks, torch)},
         "e2e": out["e2e"],
         "gpu_launches": f32["launches"],
         "clocks": f32["clocks"],
