@@ -1,7 +1,9 @@
 // Host side of libppl: the C ABI declared in include/ppl.h, device buffers, CUDA-graph
 // step chunks, and the auxiliary kernels (initial state, field export, FP64 norms).
-// The hot path is the fused step kernel of row_step.cuh (instantiated in step_fp32.cu and
-// step_fp64.cu).
+// The hot path is the fused step kernel of row_step.cuh (one column per thread; FP32, FP64
+// and the FP64 sensitivity step) and row_step_pair.cuh (FP32, two columns per thread),
+// instantiated in step_fp32.cu, step_fp64.cu and step_tangent.cu. The refinement tools
+// built on it are in tools.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
