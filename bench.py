@@ -246,6 +246,8 @@ EXPERIMENTS = {
     "gw-search": ("G_w_search", dict()),
     # pool boiling, rho_wh = 3.44 and T_h = 1.2 T_c: d^N, D^N, Q(t), time shifts
     "pool-refinement": ("pool_boiling_study", dict()),
+    # Table 3: the one-dimensional boiling-like problem, L = 160 ... 2560, both parameter sets
+    "stefan-refinement": ("stefan_study", dict()),
     # the batched refinement sequence against stepping its handles one after another
     "batch-throughput": ("batch_throughput", dict()),
     # the FP32 path against the FP64 path, per field, on the four synthetic cases
@@ -269,6 +271,8 @@ def run_experiment(args):
     t0 = time.time()
     if name == "contact-psi":
         out = {"runs": [study(value=v, **kw) for v in (4.0, 2.3, 1.7)]}
+    elif name == "stefan-refinement":
+        out = {"runs": [study(param_set=k, **kw) for k in (1, 2)]}
     else:
         out = study(**kw)
     out = {"experiment": name, "wall_seconds": time.time() - t0, **out}

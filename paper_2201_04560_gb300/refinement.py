@@ -96,13 +96,12 @@ def droplet_vaporization_study(meshes=(128, 256, 512), R0=20.0, T_ratio=0.8, Tv_
     R = [[] for _ in meshes]
     t = []
     t0 = time.perf_counter()
-    outer = coarse_steps // per_outer
-    for k in range(1, outer + 1):
-        batch.step(1)
-        if k % every == 0:
-            t.append(k * per_outer)
-            for i, (s, n) in enumerate(zip(sims, meshes)):
-                R[i].append(math.sqrt(s.phase_area(mid - band, mid + band) / math.pi) * base_n / n)
+    outer = (coarse_steps // per_outer) // every * every
+    for k in range(every, outer + 1, every):  # whole sampling intervals per call: graph replays
+        batch.step(every)
+        t.append(k * per_outer)
+        for i, (s, n) in enumerate(zip(sims, meshes)):
+            R[i].append(math.sqrt(s.phase_area(mid - band, mid + band) / math.pi) * base_n / n)
     wall = time.perf_counter() - t0
     nodes = sum(n * n * s for n, s in zip(meshes, subs)) * outer
     batch.close()
@@ -253,15 +252,14 @@ def pool_boiling_study(meshes=(160, 240, 360, 540), rho_wh=3.44, Th_ratio=1.2, c
     Q = [[] for _ in meshes]
     t = []
     t0 = time.perf_counter()
-    for k in range(1, coarse_steps // subs[0] + 1):
-        batch.step(1)
-        if k % every == 0:
-            t.append(k * subs[0])
-            for i in range(len(meshes) - 1):
-                for f in ("rho", "T"):
-                    terms[f][i].append(ppl.cross_norm(sims[i], sims[i + 1], f))
-            for i, s in enumerate(sims):
-                Q[i].append(s.wall_heat_flux(2))
+    for k in range(every, coarse_steps // subs[0] + 1, every):
+        batch.step(every)
+        t.append(k * subs[0])
+        for i in range(len(meshes) - 1):
+            for f in ("rho", "T"):
+                terms[f][i].append(ppl.cross_norm(sims[i], sims[i + 1], f))
+        for i, s in enumerate(sims):
+            Q[i].append(s.wall_heat_flux(2))
     wall = time.perf_counter() - t0
     batch.close()
     for s in sims:
@@ -284,6 +282,66 @@ def pool_boiling_study(meshes=(160, 240, 360, 540), rho_wh=3.44, Th_ratio=1.2, c
     Q = [[q * (n / base_n) ** 3 for q in series] for series, n in zip(Q, meshes)]
     return {"meshes": list(meshes), "substeps": subs, "launch_rows": shapes, "t": t, "d": d, "D": D, "Q": Q,
             "shifts": shifts, "seconds": wall, "rho_wh": rho_wh, "Th_ratio": Th_ratio}
+
+
+def _front(sim, rho_mid):
+    """Interface position of a strip (Sec. 4.2): where the y-mean density first rises
+    through rho_mid, by linear interpolation, in nodes from the wall at x = 0."""
+    prof = sim.fields()["rho"].mean(axis=0)
+    i = int(np.argmax(prof > rho_mid))
+    if i == 0:
+        return float("nan")
+    return float(i - 1 + (rho_mid - prof[i - 1]) / (prof[i] - prof[i - 1]))
+
+
+def stefan_study(param_set=2, meshes=(160, 320, 640, 1280, 2560), coarse_steps=20000, sample_every=200,
+                 precision="fp32", autotune_steps=64):
+    """Sec. 4.2, Table 3: the one-dimensional boiling-like problem on meshes of L nodes along
+    x (4 nodes across, y periodic), all run as one batch with dt ~ dx^2. Liquid at T_sat =
+    0.86 T_c, the psi-based hydrophobic wall at x = 0 held at T_w = 0.9 T_c, outflow at the
+    far end, a vapour layer of 10 / 160 of the length. param_set 1: c_v = 5 and both
+    diffusivities 0.3 (Ja = 0.038); 2: c_v = 10, lambda_l = 15, lambda_v = 1 (Ja = 0.076).
+    Returns the interface position s(t) per mesh in first-mesh nodes and the relative change
+    of Eq. (relative-change-R) form between successive meshes, with observed orders."""
+    base_n = meshes[0]
+    T_ratio = 0.86
+    Tc, rv, rl = coexistence(T_ratio)
+    sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], T_ratio * Tc)
+    if param_set == 1:
+        cv, lam_v, lam_l = 5.0, 0.3 * rv * 5.0, 0.3 * rl * 5.0
+    else:
+        cv, lam_v, lam_l = 10.0, 1.0, 15.0
+    kw = dict(cv=cv, lambda_v=lam_v, lambda_l=lam_l, dT_ratio=0.04, T_ratio=T_ratio, precision=precision)
+    n_vap = 10.0 / 160.0
+    base, _ = W.stefan_strip(Tc, rv, rl, sigma, nx=base_n, ny=4, n_vapour=n_vap * base_n, **kw)
+    subs = substeps(meshes, base_n)
+    if sample_every % subs[0]:
+        raise ValueError("sample_every must be a multiple of %d coarse steps" % subs[0])
+    sims = []
+    for n in meshes:
+        r = n / base_n
+        c, Tcn = _refined(base, base_n, n, T_ratio)
+        c["ny"] = 4  # the problem is one-dimensional: refine along x only
+        _, ic = W.stefan_strip(Tcn, rv, rl, c["sigma"], nx=n, ny=4, n_vapour=n_vap * n, width=2.0 * r, **kw)
+        sims.append(ppl.Simulation(c, *ic))
+    batch, shapes = _batch(sims, subs, autotune_steps)
+    mid = 0.5 * (rv + rl)
+    every = sample_every // subs[0]
+    s_t, t = [[] for _ in meshes], []
+    t0 = time.perf_counter()
+    for k in range(every, coarse_steps // subs[0] + 1, every):
+        batch.step(every)
+        t.append(k * subs[0])
+        for i, (sim, n) in enumerate(zip(sims, meshes)):
+            s_t[i].append(_front(sim, mid) * base_n / n)
+    wall = time.perf_counter() - t0
+    batch.close()
+    for sim in sims:
+        sim.close()
+    ds = [ppl.relative_change(s_t[i], s_t[i + 1]) for i in range(len(meshes) - 1)]
+    orders = [math.log(ds[i] / ds[i + 1]) / math.log(meshes[i + 2] / meshes[i + 1]) for i in range(len(ds) - 1)]
+    return {"param_set": param_set, "meshes": list(meshes), "substeps": subs, "launch_rows": shapes, "t": t,
+            "s": s_t, "delta_s": ds, "orders": orders, "seconds": wall}
 
 
 def fp32_error_study(steps_scale=1.0):

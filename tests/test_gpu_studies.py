@@ -52,3 +52,13 @@ def test_pool_boiling_study_small(R):
         assert 0.0 <= out["D"][f][0] < 1.0
     assert np.all(np.isfinite(np.array(out["Q"])))
     assert len(out["shifts"]) == 1 and abs(out["shifts"][0]["delta"]) <= 128
+
+
+def test_stefan_study_small(R):
+    out = R.stefan_study(param_set=2, meshes=(80, 160), coarse_steps=400, sample_every=40, autotune_steps=0)
+    assert out["substeps"] == [1, 4]
+    assert len(out["s"][0]) == len(out["s"][1]) == 10
+    s0, s1 = np.array(out["s"][0]), np.array(out["s"][1])
+    assert np.all(np.isfinite(s0)) and np.all(np.isfinite(s1))
+    assert np.all((s0 > 0) & (s0 < 80)) and abs(s0[-1] - s1[-1]) < 3.0
+    assert 0.0 <= out["delta_s"][0] < 0.5
