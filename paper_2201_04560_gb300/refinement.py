@@ -295,14 +295,18 @@ def _front(sim, rho_mid):
 
 
 def stefan_study(param_set=2, meshes=(160, 320, 640, 1280, 2560), coarse_steps=20000, sample_every=200,
-                 precision="fp32", autotune_steps=64):
+                 precision="fp64", autotune_steps=64):
     """Sec. 4.2, Table 3: the one-dimensional boiling-like problem on meshes of L nodes along
     x (4 nodes across, y periodic), all run as one batch with dt ~ dx^2. Liquid at T_sat =
     0.86 T_c, the psi-based hydrophobic wall at x = 0 held at T_w = 0.9 T_c, outflow at the
     far end, a vapour layer of 10 / 160 of the length. param_set 1: c_v = 5 and both
     diffusivities 0.3 (Ja = 0.038); 2: c_v = 10, lambda_l = 15, lambda_v = 1 (Ja = 0.076).
     Returns the interface position s(t) per mesh in first-mesh nodes and the relative change
-    of Eq. (relative-change-R) form between successive meshes, with observed orders."""
+    of Eq. (relative-change-R) form between successive meshes, with observed orders.
+
+    FP64 by default: with dt ~ dx^2 the per-step change of T and rho on the finest meshes
+    (256 steps per coarse step at 2560) falls to tens of FP32 ulps of the stored deviations,
+    and over millions of steps the rounding drift of the FP32 path moves the front."""
     base_n = meshes[0]
     T_ratio = 0.86
     Tc, rv, rl = coexistence(T_ratio)
