@@ -358,7 +358,7 @@ int ppl_contact_angle(const double *rho, int32_t nx, int32_t ny, int side, doubl
 
 /* Rows per CTA of the fused step kernel (the grid is ceil(nx / (NT - 6)) strips of
  * columns x ceil(ny / rows) row blocks; every CTA recomputes 6 halo rows). rows = 0
- * restores the default: one wave of resident CTAs over the rows, at least 8 rows each.
+ * restores the default: one wave of resident CTAs over the rows.
  * 1 <= rows <= ny otherwise (PPL_E_INVAL). Results do not depend on the shape except
  * through the rounding of the domain-mass sum of Eq. (gravitational_force), which is
  * summed per CTA (last-bit differences of rho_bar where gravity is on). Drops the

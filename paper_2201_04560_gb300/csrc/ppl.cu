@@ -485,7 +485,7 @@ int upload_state(ppl_sim *h, const double *rho0, const double *ux0, const double
   return PPL_OK;
 }
 
-// default launch shape: one wave of resident CTAs over the rows, at least 8 rows each
+// default launch shape: one wave of resident CTAs over the rows
 int default_rows(const ppl_sim *h) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -495,8 +495,7 @@ int default_rows(const ppl_sim *h) {
   const int strips = (h->nx + h->var.width - 1) / h->var.width;
   int yblocks = slots / strips;
   if (yblocks < 1) yblocks = 1;
-  int H = (h->ny + yblocks - 1) / yblocks;
-  return H < 8 ? 8 : H;
+  return (h->ny + yblocks - 1) / yblocks;  // small grids get short blocks: more CTAs in flight
 }
 
 int check_status(ppl_sim *h) {
@@ -993,8 +992,7 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   const int strips = (cfg->nx + var.width - 1) / var.width;
   int yblocks = slots / strips;
   if (yblocks < 1) yblocks = 1;
-  int H = (cfg->ny + yblocks - 1) / yblocks;
-  if (H < 8) H = 8;
+  const int H = (cfg->ny + yblocks - 1) / yblocks;
   const dim3 grid(strips, (cfg->ny + H - 1) / H);
   if ((long long)grid.x * grid.y > kNoAllocMaxCtas) return PPL_E_INVAL;  // beyond the static scratch
   // parameters of this configuration (a stack handle carries no device memory)

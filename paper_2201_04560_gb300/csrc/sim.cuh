@@ -74,7 +74,7 @@ int launch_step(ppl_sim *h, bool energy);
 bool energy_at(const ppl_sim *h, int64_t step);
 // synchronises the handle's stream and maps the device status word to PPL_OK / PPL_E_NUMERIC
 int check_status(ppl_sim *h);
-// default rows per CTA: one wave of resident CTAs over the rows, at least 8 rows each
+// default rows per CTA: one wave of resident CTAs over the rows
 int default_rows(const ppl_sim *h);
 
 template <typename real>
