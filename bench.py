@@ -252,9 +252,56 @@ EXPERIMENTS = {
     "batch-throughput": ("batch_throughput", dict()),
     # the FP32 path against the FP64 path, per field, on the four synthetic cases
     "fp32-error": ("fp32_error_study", dict()),
+    # MLUPS and HBM fraction of the step on each synthetic case, FP32 and FP64
+    "cases": ("bench.case_throughput", dict()),
     # sigma and kappa of the 192^2 mesh tuned on the lattice with sensitivity runs (Sec. 3.2)
     "calibration": ("calibration.calibrate_mesh", dict(n_base=128, n=192)),
 }
+
+
+def case_throughput():
+    """Node updates per second of the fused step on the synthetic cases shaped like the paper's
+    (the static droplet, the Stefan strip, the droplet in superheated vapour, pool boiling),
+    FP32 and FP64, default launch shape and autotuned, with the fraction of the HBM roofline
+    (80 / 160 algorithmic bytes per node over the measured copy bandwidth). The small cases fit
+    in L2 and are launch- and latency-bound; only pool boiling is HBM-sized."""
+    import torch
+    import workloads as W
+    from paper_2201_04560_gb300 import ppl
+    a, b, R, om = 3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344
+    Tc = ppl.tc(a, b, R)
+    rv8, rl8, _ = ppl.maxwell(a, b, R, om, 0.8 * Tc)
+    rv6, rl6, _ = ppl.maxwell(a, b, R, om, 0.86 * Tc)
+    s86 = ppl.sigma_for(a, b, R, om, -1.0, 0.86 * Tc)
+    cases = {
+        "static droplet 64x64": lambda p: W.static_droplet(Tc, rv8, rl8, nx=64, ny=64, precision=p),
+        "Stefan strip 1024x4": lambda p: W.stefan_strip(Tc, rv6, rl6, s86, nx=1024, ny=4, precision=p),
+        "droplet vaporization 256x256": lambda p: W.droplet_vaporization(Tc, rv8, rl8, 0.1, nx=256, ny=256,
+                                                                        R0=40.0, iso_steps=2000, precision=p),
+        "pool boiling 1024x2048": lambda p: W.pool_boiling(Tc, rv6, rl6, SIGMA, nx=1024, ny=2048, g=3e-5,
+                                                          precision=p),
+    }
+    peaks, _ = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    out = {}
+    for name, make in cases.items():
+        for prec in ("fp32", "fp64"):
+            cfg, ic = make(prec)
+            nodes = cfg["nx"] * cfg["ny"]
+            steps = max(64, min(20000, int(2e10 / nodes / (1 if prec == "fp32" else 25))))
+            with ppl.Simulation(cfg, *ic) as sim:
+                if cfg["energy_on"]:
+                    sim.step(cfg["iso_steps"])  # time the coupled step, past the isothermal start
+                dt, _ = time_device(sim, steps, 32, torch)
+                rec = {"kernel": sim.kernel, "rows": sim.launch()[0], "mlups": nodes * steps / dt / 1e6}
+                rows, _ = sim.autotune(64)
+                dt2, _ = time_device(sim, steps, 32, torch)
+                rec.update(autotuned_kernel=sim.kernel, autotuned_rows=rows, autotuned_mlups=nodes * steps / dt2 / 1e6)
+            best = max(rec["mlups"], rec["autotuned_mlups"])
+            rec["hbm_frac"] = best * 1e6 * BYTES_PER_NODE[prec] / 1e9 / hbm
+            rec["steps"] = steps
+            out["%s %s" % (name, prec)] = rec
+    return out
 
 
 def run_experiment(args):
@@ -262,9 +309,12 @@ def run_experiment(args):
     name = args.experiment
     fn, kw = EXPERIMENTS[name]
     mod, _, fname = fn.rpartition(".")
-    study = getattr(importlib.import_module("paper_2201_04560_gb300." + (mod or "refinement")), fname)
+    if mod == "bench":
+        study = globals()[fname]
+    else:
+        study = getattr(importlib.import_module("paper_2201_04560_gb300." + (mod or "refinement")), fname)
     kw = dict(kw)
-    if args.coarse_steps and fname not in ("fp32_error_study", "batch_throughput"):
+    if args.coarse_steps and fname not in ("fp32_error_study", "batch_throughput", "case_throughput"):
         kw["coarse_steps"] = args.coarse_steps
     if args.precision in ("fp32", "fp64") and not mod and fname not in ("G_w_search", "fp32_error_study"):
         kw["precision"] = args.precision
