@@ -367,8 +367,8 @@ int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
 
 /* Step kernel of an FP32 handle. PPL_KERNEL_COLUMN: one column per thread (any
  * boundaries). PPL_KERNEL_PAIR: two adjacent columns per thread with packed f32x2
- * arithmetic, for domains periodic in x for both the hydrodynamics and the temperature
- * with an even nx (PPL_E_INVAL otherwise). PPL_KERNEL_AUTO (the default at ppl_init): PAIR
+ * arithmetic, for domains hydrodynamically periodic in x with an even nx (PPL_E_INVAL
+ * otherwise; the temperature may be held on the x lines). PPL_KERNEL_AUTO (the default at ppl_init): PAIR
  * where it applies, else COLUMN. FP64 and tangent handles always use the one-column
  * kernel. Resets the launch shape to its default and drops captured graphs; synchronises.
  * ppl_get_kernel returns the kernel in use. */

@@ -256,12 +256,12 @@ uint64_t hash_config(const ppl_sim *h) {
 // FP64 state carrying d/d(sigma) or d/d(kappa)
 bool is_tangent(int prec) { return prec == PPL_FP64_DSIGMA || prec == PPL_FP64_DKAPPA; }
 
-// The two-column FP32 kernel needs x periodic for the hydrodynamics and the temperature
-// (no x-boundary columns) and an even nx (8-byte aligned column pairs that never straddle
-// the periodic seam).
+// The two-column FP32 kernel needs x periodic for the hydrodynamics (no wall or outflow
+// columns; the temperature may be held on the x lines) and an even nx (8-byte aligned
+// column pairs that never straddle the periodic seam).
 bool pair_applicable(const ppl_config &c) {
   return c.precision == PPL_FP32DEV && c.hydro_bc[0] == PPL_PERIODIC && c.hydro_bc[1] == PPL_PERIODIC &&
-         c.thermal_bc[0] == PPL_T_PERIODIC && c.thermal_bc[1] == PPL_T_PERIODIC && c.nx % 2 == 0 && c.nx >= 8;
+         c.nx % 2 == 0 && c.nx >= 8;
 }
 
 // kernel: PPL_KERNEL_AUTO, PPL_KERNEL_COLUMN or PPL_KERNEL_PAIR (checked by the caller)

@@ -1,5 +1,6 @@
 // FP32 fused step with two columns per thread (packed f32x2 arithmetic) for domains that
-// are periodic in x, hydrodynamically and thermally, with an even nx.
+// are hydrodynamically periodic in x, with an even nx (the x lines may hold Dirichlet
+// temperatures).
 //
 // The same row-marching pipeline as row_step.cuh (stages S1..S4 at row lags 0..3, rings
 // of per-row quantities in shared memory), with each thread owning the adjacent columns
@@ -66,6 +67,8 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   int src0 = gx0 % P.nx;
   if (src0 < 0) src0 += P.nx;
   const int col0 = src0, col1 = src0 + 1;  // in-domain columns of the two lanes
+  // a lane on a thermally non-periodic x line (e.g. a Dirichlet ring around a periodic box)
+  const bool col_fix = (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (col0 == 0 || col1 == P.nx - 1);
   const long long plane = P.plane;
   const float rho_bar = (float)io.stats_in[0];
   const bool any_outflow = P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
@@ -263,7 +266,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
                           T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0) * nxt.div * nxt.inv_rcv;
             nxt.k1 = k1;
             Ts = T0 + k1;
-            if (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) {  // Dirichlet nodes of a y line
+            if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes of a boundary line
               float tw0, tw1;
               const bool d0 = t_fixed(P, col0, rm.src, &tw0), d1 = t_fixed(P, col1, rm.src, &tw1);
               if (d0 || d1) {
@@ -313,7 +316,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           const F2 k2 = -(cur.ux * gtx + cur.uy * gty) + (cur.lam * lap + cur.gdx * gtx + cur.gdy * gty) * cur.inv_rcv -
                         T_dpdT(P, cur.A, cur.B, P.T_ref + tm.c) * cur.div * cur.inv_rcv;
           T_new = T_new + 0.5f * (cur.k1 + k2);
-          if (!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) {  // Dirichlet nodes keep their value
+          if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes keep their value
             float tw;
             const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
             T_new = F2(d0 ? T_old.lo() : T_new.lo(), d1 ? T_old.hi() : T_new.hi());

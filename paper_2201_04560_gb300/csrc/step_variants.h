@@ -22,7 +22,7 @@ struct StepVariant {
 };
 
 StepVariant step_variant_fp32();
-StepVariant step_variant_fp32_pair();  // two columns per thread: x periodic (hydro and T), nx even
+StepVariant step_variant_fp32_pair();  // two columns per thread: hydrodynamically x-periodic, nx even
 StepVariant step_variant_fp64();
 StepVariant step_variant_tangent();  // FP64 value + derivative (Dual)
 

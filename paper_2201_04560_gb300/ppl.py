@@ -352,7 +352,7 @@ class Simulation:
 
     def select_kernel(self, kind: str = "auto"):
         """FP32 step kernel: "column" (one column per thread), "pair" (two columns per thread,
-        packed f32x2; x-periodic domains with even nx) or "auto"."""
+        packed f32x2; domains periodic in x for the flow, with even nx) or "auto"."""
         _check(self.lib.ppl_select_kernel(self.h, self.KERNELS[kind]), "ppl_select_kernel")
 
     @property

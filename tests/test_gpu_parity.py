@@ -259,7 +259,7 @@ def test_pair_kernel_selection_rules(sim_cls, th):
         assert s.kernel == "column"  # FP64
 
 
-@pytest.mark.parametrize("case", ["stefan_y", "sessile_psi", "sessile_mod"])
+@pytest.mark.parametrize("case", ["stefan_y", "sessile_psi", "sessile_mod", "vaporization_ring"])
 def test_pair_kernel_wall_rows_fp32(sim_cls, th, case):
     # the two-column kernel's row-boundary paths: a psi-based wall row held at a Dirichlet
     # temperature with an outflow row opposite (the Stefan strip turned to run along y),
@@ -270,6 +270,13 @@ def test_pair_kernel_wall_rows_fp32(sim_cls, th, case):
         cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=203, ny=8, n_vapour=10, precision="fp32")
         cfg, ic = _transpose_case(cfg, ic)
         steps = 1500
+    elif case == "vaporization_ring":
+        # temperature held on all four boundary lines of a periodic box: the x lines' Dirichlet
+        # nodes are applied lane by lane
+        rv8, rl8, _ = th[0.8]
+        cfg, ic = W.droplet_vaporization(e.Tc, rv8, rl8, 0.1, nx=130, ny=52, R0=14.0, iso_steps=40,
+                                         precision="fp32")
+        steps = 400
     else:
         cm = W.CONTACT_PSI if case == "sessile_psi" else W.CONTACT_MOD_PSI
         cfg, ic = W.sessile_droplet(e.Tc, rv, rl, th["sigma086"], nx=70, ny=41, R0=13.0, contact_model=cm,
