@@ -53,11 +53,15 @@ extern "C" {
 #define PPL_FP32DEV 1 /* FP32 arithmetic; f_i - w_i rho_ref and T - T_ref stored in FP32 */
 /* FP64 state that also carries its derivative with respect to sigma (Eq. S) or kappa
  * (Eq. Q): forward-mode (tangent-linear) sensitivity, read with ppl_tangent_fields. The
- * initial state has zero derivative. rho_bar of Eq. (gravitational_force) is taken as
- * parameter-independent (its derivative is zero whenever mass is conserved). Not accepted by
- * ppl_step_noalloc, ppl_cross_norm or ppl_wall_heat_flux; ppl_phase_area reads the values. */
+ * initial state has zero derivative; the derivative of rho_bar of Eq. (gravitational_force)
+ * is carried with it (an FP64 domain sum). Not accepted by ppl_step_noalloc, ppl_cross_norm
+ * or ppl_wall_heat_flux; ppl_phase_area reads the values. */
 #define PPL_FP64_DSIGMA 2
 #define PPL_FP64_DKAPPA 3
+/* The same in FP32 arithmetic (values stored as f_i - w_i rho_ref and T - T_ref like
+ * PPL_FP32DEV, derivatives in FP32; the domain sums and d rho_bar stay FP64). */
+#define PPL_FP32_DSIGMA 4
+#define PPL_FP32_DKAPPA 5
 
 #define PPL_PERIODIC 0 /* hydrodynamic side kinds */
 #define PPL_WALL 1     /* Zou-He no-slip wet node + psi-based adhesion (Sec. 2.2) */
@@ -178,7 +182,7 @@ int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtyp
 int ppl_populations(ppl_t *h, double *f);
 
 /* Derivatives d rho, d u_x, d u_y, d T of the current state with respect to the parameter
- * of a PPL_FP64_DSIGMA / PPL_FP64_DKAPPA handle, as host FP64 [ny][nx] arrays (NULL
+ * of a sensitivity handle (PPL_FP64_D* or PPL_FP32_D*), as host FP64 [ny][nx] arrays (NULL
  * pointers skip a field). PPL_E_INVAL for other handles. Synchronises. */
 int ppl_tangent_fields(ppl_t *h, double *drho, double *dux, double *duy, double *dT);
 
@@ -221,7 +225,7 @@ void ppl_destroy(ppl_t *h);
  * loads the library until the process exits. A launch grid of more than 4096 CTAs (the
  * default shape is one wave of resident CTAs, so only very wide grids, beyond about 4096
  * column strips of 120-122 columns, reach it) is rejected with PPL_E_INVAL before anything
- * runs. The sensitivity precisions (PPL_FP64_DSIGMA/DKAPPA) are rejected as well. The first call on each device
+ * runs; so are the sensitivity precisions. The first call on each device
  * resolves the scratch's device address and sets kernel attributes; make that first call
  * before any stream capture. All calls share the one scratch array and it keeps the last
  * call's contents (the counter is cleared by each call): calls that overlap on the GPU,

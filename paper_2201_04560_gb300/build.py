@@ -19,6 +19,7 @@ UNITS = {
     "step_fp64.cu": [],
     "step_fp32.cu": ["--use_fast_math"],
     "step_tangent.cu": [],
+    "step_tangent32.cu": ["--use_fast_math"],
 }
 SOURCES = [os.path.join(CSRC, u) for u in UNITS]
 DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("common.cuh", "dual.cuh", "lane2.cuh", "row_step.cuh", "row_step_pair.cuh", "sim.cuh", "step_variants.h")] + [

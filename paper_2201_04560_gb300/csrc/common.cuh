@@ -322,6 +322,11 @@ __device__ __forceinline__ Dual ld_real<Dual>(const void *p, long long k) {
   const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
   return Dual(v.x, v.y);
 }
+template <>
+__device__ __forceinline__ DualF ld_real<DualF>(const void *p, long long k) {
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(p) + k);
+  return DualF(v.x, v.y);
+}
 
 
 }  // namespace ppl_dev

@@ -174,7 +174,7 @@ __global__ void export_fields(const Params<real> P, const real *f, const real *T
     sy += w * pn * real(kCY[q]);
   }
   real rho_bar = (real)stats[0];
-  if constexpr (is_dual<real>::value) rho_bar = Dual(stats[0], stats[2]);  // with d rho_bar
+  if constexpr (is_dual<real>::value) rho_bar = real(stats[0], stats[2]);  // with d rho_bar
   const real Fx = -P.G * psi_c * sx + P.gx * (rho - rho_bar);
   const real Fy = -P.G * psi_c * sy + P.gy * (rho - rho_bar);
   const real ux = (jx + real(0.5) * Fx) / rho, uy = (jy + real(0.5) * Fy) / rho;
@@ -253,8 +253,13 @@ uint64_t hash_config(const ppl_sim *h) {
   return x;
 }
 
-// FP64 state carrying d/d(sigma) or d/d(kappa)
-bool is_tangent(int prec) { return prec == PPL_FP64_DSIGMA || prec == PPL_FP64_DKAPPA; }
+// a state carrying d/d(sigma) or d/d(kappa), FP64 or FP32
+bool is_tangent(int prec) {
+  return prec == PPL_FP64_DSIGMA || prec == PPL_FP64_DKAPPA || prec == PPL_FP32_DSIGMA || prec == PPL_FP32_DKAPPA;
+}
+bool is_tangent32(int prec) { return prec == PPL_FP32_DSIGMA || prec == PPL_FP32_DKAPPA; }
+// FP32 storage: f_i - w_i rho_ref and T - T_ref
+bool stores_deviation(int prec) { return prec == PPL_FP32DEV || is_tangent32(prec); }
 
 // The two-column FP32 kernel needs x periodic for the hydrodynamics (no wall or outflow
 // columns; the temperature may be held on the x lines) and an even nx (8-byte aligned
@@ -267,6 +272,7 @@ bool pair_applicable(const ppl_config &c) {
 // kernel: PPL_KERNEL_AUTO, PPL_KERNEL_COLUMN or PPL_KERNEL_PAIR (checked by the caller)
 StepVariant pick_variant(const ppl_config &c, int kernel) {
   if (c.precision == PPL_FP64) return step_variant_fp64();
+  if (is_tangent32(c.precision)) return step_variant_tangent32();
   if (c.precision != PPL_FP32DEV) return step_variant_tangent();
   const bool pair = kernel == PPL_KERNEL_PAIR || (kernel == PPL_KERNEL_AUTO && pair_applicable(c));
   return pair ? step_variant_fp32_pair() : step_variant_fp32();
@@ -343,10 +349,10 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
   P.sigma12_z = (real)(12.0 * c.sigma / (1.0 / c.s[2] - 0.5));
   P.kappa_G2 = (real)(c.kappa * c.G / 2.0);
   if constexpr (is_dual<real>::value) {  // seed the parameter the tangent is taken with
-    if (h->prec == PPL_FP64_DSIGMA) {
+    if (h->prec == PPL_FP64_DSIGMA || h->prec == PPL_FP32_DSIGMA) {
       P.sigma12_e.d = 12.0 / (1.0 / c.s[1] - 0.5);
       P.sigma12_z.d = 12.0 / (1.0 / c.s[2] - 0.5);
-    } else if (h->prec == PPL_FP64_DKAPPA) {
+    } else {
       P.kappa_G2.d = c.G / 2.0;
     }
   }
@@ -367,8 +373,8 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
     P.T_w[s] = tw[s];
     P.T_dir[s] = td[s];
   }
-  P.rho_ref = h->prec == PPL_FP32DEV ? (real)c.rho_ref : (real)0;
-  P.T_ref = h->prec == PPL_FP32DEV ? (real)c.T_ref : (real)0;
+  P.rho_ref = stores_deviation(h->prec) ? (real)c.rho_ref : (real)0;
+  P.T_ref = stores_deviation(h->prec) ? (real)c.T_ref : (real)0;
   P.inv_nodes = 1.0 / (double)P.plane;
 }
 
@@ -398,9 +404,10 @@ int launch_step_t(ppl_sim *h, bool energy) {
 }
 
 int launch_step(ppl_sim *h, bool energy) {
-  return h->prec == PPL_FP64      ? launch_step_t<double>(h, energy)
-         : h->prec == PPL_FP32DEV ? launch_step_t<float>(h, energy)
-                                  : launch_step_t<Dual>(h, energy);
+  return h->prec == PPL_FP64        ? launch_step_t<double>(h, energy)
+         : h->prec == PPL_FP32DEV   ? launch_step_t<float>(h, energy)
+         : is_tangent32(h->prec)    ? launch_step_t<DualF>(h, energy)
+                                    : launch_step_t<Dual>(h, energy);
 }
 
 bool energy_at(const ppl_sim *h, int64_t step) { return h->cfg.energy_on && step >= h->cfg.iso_steps; }
@@ -442,9 +449,10 @@ int run_stats(ppl_sim *h, double *stats_dst) {
 }
 
 int stats(ppl_sim *h, double *stats_dst) {
-  return h->prec == PPL_FP64      ? run_stats<double>(h, stats_dst)
-         : h->prec == PPL_FP32DEV ? run_stats<float>(h, stats_dst)
-                                  : run_stats<Dual>(h, stats_dst);
+  return h->prec == PPL_FP64        ? run_stats<double>(h, stats_dst)
+         : h->prec == PPL_FP32DEV   ? run_stats<float>(h, stats_dst)
+         : is_tangent32(h->prec)    ? run_stats<DualF>(h, stats_dst)
+                                    : run_stats<Dual>(h, stats_dst);
 }
 
 template <typename real>
@@ -470,6 +478,7 @@ int upload_state(ppl_sim *h, const double *rho0, const double *ux0, const double
   CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
   int rc = h->prec == PPL_FP64      ? upload_state_t<double>(h, rho0, ux0, uy0, T0)
            : h->prec == PPL_FP32DEV ? upload_state_t<float>(h, rho0, ux0, uy0, T0)
+           : is_tangent32(h->prec)  ? upload_state_t<DualF>(h, rho0, ux0, uy0, T0)
                                     : upload_state_t<Dual>(h, rho0, ux0, uy0, T0);
   if (rc) return rc;
   rc = stats(h, h->stats[0]);
@@ -630,7 +639,10 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
   h->nx = cfg->nx;
   h->ny = cfg->ny;
   h->N = (long long)cfg->nx * cfg->ny;
-  h->rsz = h->prec == PPL_FP64 ? 8 : h->prec == PPL_FP32DEV ? 4 : sizeof(Dual);
+  h->rsz = h->prec == PPL_FP64        ? 8
+           : h->prec == PPL_FP32DEV   ? 4
+           : is_tangent32(h->prec)    ? sizeof(DualF)
+                                      : sizeof(Dual);
   for (int s = 0; s < 4; ++s) {
     const int len = s < 2 ? cfg->ny : cfg->nx;
     if (cfg->rho_w[s]) h->h_rho_w[s].assign(cfg->rho_w[s], cfg->rho_w[s] + len);
@@ -697,9 +709,12 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
       auto put_real = [&](const std::vector<double> &v, const void **dst) {
         if (v.empty()) return;
         for (size_t i = 0; i < len; ++i) {
-          if (h->rsz == 8) {
+          if (h->prec == PPL_FP64) {
             memcpy(&host[off + i * 8], &v[i], 8);
-          } else if (h->rsz == sizeof(Dual)) {
+          } else if (is_tangent32(h->prec)) {
+            const DualF x(v[i]);
+            memcpy(&host[off + i * sizeof(DualF)], &x, sizeof(DualF));
+          } else if (is_tangent(h->prec)) {
             const Dual x(v[i]);
             memcpy(&host[off + i * sizeof(Dual)], &x, sizeof(Dual));
           } else {
@@ -724,6 +739,8 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
     fill_params<double>(h, h->pd, (const double *const *)rw, (const double *const *)tw, td);
   else if (h->prec == PPL_FP32DEV)
     fill_params<float>(h, h->pf, (const float *const *)rw, (const float *const *)tw, td);
+  else if (is_tangent32(h->prec))
+    fill_params<DualF>(h, h->ptf, (const DualF *const *)rw, (const DualF *const *)tw, td);
   else
     fill_params<Dual>(h, h->pt, (const Dual *const *)rw, (const Dual *const *)tw, td);
 
@@ -790,6 +807,10 @@ static int export_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int d
     export_fields<float><<<nb, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur],
                                                    (const float *)h->T[h->cur], h->stats[h->cur], rho, ux, uy, T,
                                                    dtype);
+  else if (is_tangent32(h->prec))
+    export_fields<DualF><<<nb, nt, 0, h->stream>>>(h->ptf, (const DualF *)h->f[h->cur],
+                                                   (const DualF *)h->T[h->cur], h->stats[h->cur], rho, ux, uy, T,
+                                                   dtype);
   else
     export_fields<Dual><<<nb, nt, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], (const Dual *)h->T[h->cur],
                                                   h->stats[h->cur], rho, ux, uy, T, dtype);
@@ -838,6 +859,8 @@ int ppl_populations(ppl_t *h, double *f) {
     export_populations<double><<<blocks, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], d);
   else if (h->prec == PPL_FP32DEV)
     export_populations<float><<<blocks, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], d);
+  else if (is_tangent32(h->prec))
+    export_populations<DualF><<<blocks, nt, 0, h->stream>>>(h->ptf, (const DualF *)h->f[h->cur], d);
   else
     export_populations<Dual><<<blocks, nt, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], d);
   int rc = cuda_err(cudaGetLastError());

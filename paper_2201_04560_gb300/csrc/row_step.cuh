@@ -194,7 +194,7 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   const bool col_bnd = cm.src == 0 || cm.src == P.nx - 1;  // node may sit on an x boundary line
   const long long plane = P.plane;
   real rho_bar = real(io.stats_in[0]);
-  if constexpr (is_dual<real>::value) rho_bar = Dual(io.stats_in[0], io.stats_in[2]);
+  if constexpr (is_dual<real>::value) rho_bar = real(io.stats_in[0], io.stats_in[2]);
   const bool xwall_strip = (P.hbc[0] == WALL && x0 - 3 < 0) || (P.hbc[1] == WALL && x0 + W + 3 > P.nx - 1);
   const bool xout_strip = (P.hbc[0] == OUTFLOW && x0 - 3 <= 0) || (P.hbc[1] == OUTFLOW && x0 + W + 3 >= P.nx - 1);
   const bool any_outflow = P.hbc[0] == OUTFLOW || P.hbc[1] == OUTFLOW || P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;

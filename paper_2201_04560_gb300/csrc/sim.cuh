@@ -47,7 +47,8 @@ struct ppl_sim {
   int stats_blocks = 0;
   Params<double> pd;
   Params<float> pf;
-  Params<Dual> pt;  // tangent modes
+  Params<Dual> pt;    // FP64 tangent modes
+  Params<DualF> ptf;  // FP32 tangent modes
   uint64_t cfg_hash = 0;
 };
 
@@ -62,8 +63,9 @@ int cuda_err(cudaError_t e);
     if (_rc != PPL_OK) return _rc;              \
   } while (0)
 
-// FP64 state carrying d/d(sigma) or d/d(kappa)
+// a state carrying d/d(sigma) or d/d(kappa) (FP64 or FP32)
 bool is_tangent(int prec);
+bool is_tangent32(int prec);
 // the two-column FP32 kernel applies (x periodic for rho and T, even nx)
 bool pair_applicable(const ppl_config &c);
 // step kernel variant for a configuration and PPL_KERNEL_* choice
@@ -85,5 +87,7 @@ template <>
 inline const Params<float> &params_of<float>(const ppl_sim *h) { return h->pf; }
 template <>
 inline const Params<Dual> &params_of<Dual>(const ppl_sim *h) { return h->pt; }
+template <>
+inline const Params<DualF> &params_of<DualF>(const ppl_sim *h) { return h->ptf; }
 
 }  // namespace ppl_host

@@ -11,6 +11,8 @@ constexpr int kNT64 = 128;
 constexpr int kPF64 = 1;
 constexpr int kNTD = 128;  // tangent (Dual) step
 constexpr int kPFD = 1;
+constexpr int kNTDF = 128;  // FP32 tangent (DualF) step
+constexpr int kPFDF = 1;
 constexpr int kNTP = 64;   // FP32 two-column kernel: threads per CTA (2 kNTP columns)
 constexpr int kPFP = 1;
 
@@ -24,6 +26,7 @@ struct StepVariant {
 StepVariant step_variant_fp32();
 StepVariant step_variant_fp32_pair();  // two columns per thread: hydrodynamically x-periodic, nx even
 StepVariant step_variant_fp64();
-StepVariant step_variant_tangent();  // FP64 value + derivative (Dual)
+StepVariant step_variant_tangent();    // FP64 value + derivative (Dual)
+StepVariant step_variant_tangent32();  // FP32 value + derivative (DualF)
 
 }  // namespace ppl_dev

@@ -540,6 +540,9 @@ int ppl_phase_area(ppl_t *h, double rho_lo, double rho_hi, double *area) {
   else if (h->prec == PPL_FP32DEV)
     phase_area_partials<float><<<nblk, 256, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], rho_lo, inv,
                                                             h->partials);
+  else if (is_tangent32(h->prec))
+    phase_area_partials<DualF><<<nblk, 256, 0, h->stream>>>(h->ptf, (const DualF *)h->f[h->cur], rho_lo, inv,
+                                                            h->partials);
   else
     phase_area_partials<Dual><<<nblk, 256, 0, h->stream>>>(h->pt, (const Dual *)h->f[h->cur], rho_lo, inv,
                                                            h->partials);

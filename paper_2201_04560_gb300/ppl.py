@@ -16,8 +16,9 @@ from . import build as _build
 PPL_OK, PPL_E_INVAL, PPL_E_CUDA, PPL_E_NUMERIC, PPL_E_TIMEOUT, PPL_E_IO, PPL_E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 PPL_FP64, PPL_FP32DEV = 0, 1
 PPL_FP64_DSIGMA, PPL_FP64_DKAPPA = 2, 3  # FP64 state + its derivative w.r.t. sigma / kappa
+PPL_FP32_DSIGMA, PPL_FP32_DKAPPA = 4, 5  # the same in FP32 arithmetic and deviation storage
 PRECISIONS = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV, "fp64_dsigma": PPL_FP64_DSIGMA,
-              "fp64_dkappa": PPL_FP64_DKAPPA}
+              "fp64_dkappa": PPL_FP64_DKAPPA, "fp32_dsigma": PPL_FP32_DSIGMA, "fp32_dkappa": PPL_FP32_DKAPPA}
 FLAG_PSI_NEG, FLAG_NAN, FLAG_RHO_NONPOS = 1, 2, 4
 
 _D = ctypes.c_double
@@ -307,7 +308,7 @@ class Simulation:
         return dict(zip(("rho", "ux", "uy", "T"), out))
 
     def tangent_fields(self):
-        """d(rho, u_x, u_y, T)/d(parameter) of a fp64_dsigma / fp64_dkappa simulation."""
+        """d(rho, u_x, u_y, T)/d(parameter) of a sensitivity simulation (fp64_d* / fp32_d*)."""
         out = [np.empty((self.ny, self.nx)) for _ in range(4)]
         _check(self.lib.ppl_tangent_fields(self.h, *[_ptr(a) for a in out]), "ppl_tangent_fields")
         return dict(zip(("rho", "ux", "uy", "T"), out))

@@ -47,7 +47,7 @@ def run(ppl, cfg, ic, steps, **over):
     with ppl.Simulation(c, *ic) as s:
         s.step(steps)
         out = s.fields()
-        if c.get("precision", "fp64").startswith("fp64_d"):
+        if "_d" in c.get("precision", "fp64"):
             out["d"] = s.tangent_fields()
     return out
 
@@ -180,3 +180,18 @@ def test_autograd_function_gradient_and_descent(ppl):
         g = q.grad
         q2 = q - 0.5 * L0 / (g @ g) * g  # half a Gauss-Newton-sized step along -grad
     assert float(loss(q2)) < float(L0)
+
+
+@pytest.mark.parametrize("name", ["droplet", "vaporization", "pool"])
+@pytest.mark.parametrize("param", ["sigma", "kappa"])
+def test_fp32_tangent_tracks_fp64_tangent(ppl, th, name, param):
+    # FP32 forward (deviation storage, FP64 domain sums) against the FP64 sensitivity run:
+    # values within the FP32 budget, derivatives within 1e-3 in the L1 norm of the field
+    cfg, ic, steps = make_case(th, name)
+    t64 = run(ppl, cfg, ic, steps, precision="fp64_d" + param)
+    t32 = run(ppl, cfg, ic, steps, precision="fp32_d" + param)
+    for f in ("rho", "T"):
+        assert float(np.abs(t32[f] - t64[f]).sum() / np.abs(t64[f]).sum()) <= 1e-4
+    for f in ("rho", "ux", "uy"):
+        ref = t64["d"][f]
+        assert float(np.abs(t32["d"][f] - ref).sum() / np.abs(ref).sum()) <= 1e-3, f
