@@ -45,6 +45,12 @@ struct Params {
   double inv_nodes;  // 1 / (nx ny)
   int mod_psi;       // wall adhesion: 0 psi-based, 1 modified psi-based
   real Gw_over_G;    // G_w / G of the modified model
+  // coefficients of collide() with the relaxation rates and the row norms of M^-1 folded in
+  real c1n, c1q, c1u, c1f;  // energy e:         a_1 = dm_1 / 36
+  real c2n, c2q, c2u, c2f;  // energy square:    a_2 = dm_2 / 36
+  real c4n, c4f, c6n, c6f;  // energy fluxes:    a_4 = dm_4 / 12, a_6 = dm_6 / 12
+  real e_c0, e_c1;          // s_eta / 4 = 1 / (e_c0 + e_c1 rho) for a density-dependent viscosity
+  real e_const;             // s_eta / 4 otherwise
 };
 
 struct StepIO {
@@ -70,28 +76,32 @@ __device__ __forceinline__ real wgt(int i) {
 
 // ---- Peng-Robinson EOS (Eq. peng-robinson) and the psi argument (Eq. psi) ----
 // (PT: the parameter precision; real: the value type, PT itself or two packed FP32 lanes)
+// The pressure is split as p = T A(rho) - alpha(T) B(rho) with A = rho R / (1 - b rho),
+// B = a rho^2 / (1 + 2 b rho - b^2 rho^2) and alpha = (1 + k (1 - sqrt(T/Tc)))^2; the
+// compression term of the energy equation is then T (dp/dT)_rho = T A + E(rho, T) with
+// E = -T alpha'(T) B = k B alpha^(1/2) sqrt(T/Tc).
 template <typename PT, typename real>
-__device__ __forceinline__ real pr_alpha_root(const Params<PT> &P, real T) {
-  return real(1) + P.k * (real(1) - sqrt(T) * P.sqrt_Tc_inv);
+__device__ __forceinline__ void pr_parts(const Params<PT> &P, real rho, real *A, real *B) {
+  const real omb = real(1) - P.b * rho;
+  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
+  const real inv = real(1) / (omb * den);  // one division for both parts
+  *A = rho * P.R * den * inv;
+  *B = P.a * rho * rho * omb * inv;
+}
+// psi argument 2 (p - rho/3) / G of Eq. psi, with the parts A, B, E of the same (rho, T)
+template <typename PT, typename real>
+__device__ __forceinline__ real psi_arg_eos(const Params<PT> &P, real rho, real T, real *A, real *B, real *E) {
+  const real st = sqrt(T) * P.sqrt_Tc_inv;
+  const real ar = real(1) + P.k * (real(1) - st);
+  pr_parts(P, rho, A, B);
+  *E = P.k * *B * ar * st;
+  const real p = T * *A - ar * ar * *B;
+  return (p - rho * (real(1) / real(3))) * P.twoG_inv;
 }
 template <typename PT, typename real>
 __device__ __forceinline__ real psi_arg(const Params<PT> &P, real rho, real T) {
-  // p = rho R T / (1 - b rho) - a alpha rho^2 / (1 + 2 b rho - b^2 rho^2), over one denominator
-  const real ar = pr_alpha_root(P, T);
-  const real omb = real(1) - P.b * rho;
-  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
-  const real p = (rho * P.R * T * den - P.a * ar * ar * rho * rho * omb) / (omb * den);
-  return (p - rho * (real(1) / real(3))) * P.twoG_inv;
-}
-// rho-only parts of T (dp/dT)_rho = T A(rho) + k B(rho) (1 + k(1 - sqrt(T/Tc))) sqrt(T/Tc),
-// with A = rho R / (1 - b rho) and B = a rho^2 / (1 + 2 b rho - b^2 rho^2) (one division)
-template <typename PT, typename real>
-__device__ __forceinline__ void dpdT_parts(const Params<PT> &P, real rho, real *A, real *B) {
-  const real omb = real(1) - P.b * rho;
-  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
-  const real inv = real(1) / (omb * den);
-  *A = rho * P.R * den * inv;
-  *B = P.a * rho * rho * omb * inv;
+  real A, B, E;
+  return psi_arg_eos(P, rho, T, &A, &B, &E);
 }
 template <typename PT, typename real>
 __device__ __forceinline__ real T_dpdT(const Params<PT> &P, real A, real B, real T) {
@@ -245,72 +255,66 @@ __device__ __forceinline__ void zou_he(int side, real f[9], real Jx, real Jy) {
 }
 
 // ---- MRT collision in deviation form (Eqs. collisionMRT, li_source_terms, S, C) ----
-// fd: deviations f~ on entry, post-collision deviations on exit. rho = rho_ref + sum f~.
+// fd: deviations f~ on entry, post-collision deviations on exit. rho = rho_ref + sum f~ (the
+// value of the row's first stage), (ux, uy) the half-force velocity of the same populations
+// (Eq. DensityAndVelocityRelationToF), F the total force, fm2 = |F^m|^2 / psi^2, Q of Eq. Q
+// as qs = Qxx + Qyy, qd = Qxx - Qyy and qxy = Qxy, e = s_eta / 4.
+//
+// The moment increments dm = -Lambda (m - m^eq) + (I - Lambda/2) S + C are formed in closed
+// form, with the rows of M of Sec. 2 (e: -4, -1 x4, 2 x4; eps: 4, -2 x4, 1 x4):
+//  - momentum: m_j - rho u = -F/2 by the definition of u, so dm_jx = Fx and dm_jy = Fy
+//    whatever s_j is;
+//  - e and eps: with delta = sum f~, the rho_ref w_i parts cancel and the non-equilibrium
+//    parts m_e - m_e^eq = m~_e + 2 delta - 3 rho u^2 and m_eps - m_eps^eq = m~_eps - delta +
+//    3 rho u^2 reduce to -2 f~0 + (f~1 + .. + f~4) + 4 (f~5 + .. + f~8) - 3 rho u^2 and
+//    3 (f~0 - (f~1 + .. + f~4) + rho u^2), free of the mass sum;
+//  - dm_0 = 0, so f* = f + M^-1 dm leaves the mass untouched by construction.
+// M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); its row norms and the
+// relaxation rates are folded into the coefficients Params::c* (a_k = dm_k / |M_k|^2), and
+// the sums over the nine rows of M^T are factored into shared pairs.
 template <typename PT, typename real>
-__device__ __forceinline__ void collide(const Params<PT> &P, real fd[9], real rho, real delta, real ux,
-                                        real uy, real Fx, real Fy, real Fm2_over_psi2, real Qxx, real Qyy,
-                                        real Qxy, real s_eta) {
-  // deviation moments m~ = M f~ (rows of M, Sec. 2)
-  const real ax = fd[1] + fd[2] + fd[3] + fd[4];
-  const real dg = fd[5] + fd[6] + fd[7] + fd[8];
-  const real m1 = -real(4) * fd[0] - ax + real(2) * dg;
-  const real m2 = real(4) * fd[0] - real(2) * ax + dg;
-  const real m3 = fd[1] - fd[3] + fd[5] - fd[6] - fd[7] + fd[8];
-  const real m4 = -real(2) * fd[1] + real(2) * fd[3] + fd[5] - fd[6] - fd[7] + fd[8];
-  const real m5 = fd[2] - fd[4] + fd[5] + fd[6] - fd[7] - fd[8];
-  const real m6 = -real(2) * fd[2] + real(2) * fd[4] + fd[5] + fd[6] - fd[7] - fd[8];
-  const real m7 = fd[1] - fd[2] + fd[3] - fd[4];
-  const real m8 = fd[5] - fd[6] + fd[7] - fd[8];
-  // non-equilibrium parts m - m^eq (m^eq = M f^eq of Eq. EquilibriumDistribution);
-  // the rho_ref w_i part contributes (rho_ref, -2 rho_ref, rho_ref, 0, ...) to m
-  const real u2 = ux * ux + uy * uy;
-  const real ru2 = rho * u2;
-  const real n1 = m1 + real(2) * delta - real(3) * ru2;
-  const real n2 = m2 - delta + real(3) * ru2;
-  const real n3 = m3 - rho * ux;
-  const real n4 = m4 + rho * ux;
-  const real n5 = m5 - rho * uy;
-  const real n6 = m6 + rho * uy;
-  const real n7 = m7 - rho * (ux * ux - uy * uy);
-  const real n8 = m8 - rho * ux * uy;
-  // Li forcing S (Eq. S, sigma term with |F^m|^2) and the kappa correction C (Eq. C)
+__device__ __forceinline__ void collide(const Params<PT> &P, real fd[9], real rho, real ux, real uy, real Fx,
+                                        real Fy, real fm2, real qs, real qd, real qxy, real e) {
+  const real s13 = fd[1] + fd[3], d13 = fd[1] - fd[3];
+  const real s24 = fd[2] + fd[4], d24 = fd[2] - fd[4];
+  const real s57 = fd[5] + fd[7], d57 = fd[5] - fd[7];
+  const real s68 = fd[6] + fd[8], d68 = fd[6] - fd[8];
+  const real ax = s13 + s24, dg = s57 + s68;
+  const real jx = rho * ux, jy = rho * uy;  // rho u = m_j + F/2
+  const real ru2 = jx * ux + jy * uy;
+  const real ne = real(4) * dg + (ax - real(2) * fd[0]) - real(3) * ru2;  // m_e - m_e^eq
+  const real nz = (fd[0] - ax) + ru2;                                     // (m_eps - m_eps^eq) / 3
+  const real nqx = ((d57 - d68) - real(2) * d13) + jx;                    // m_qx^eq = -rho ux
+  const real nqy = ((d57 + d68) - real(2) * d24) + jy;
+  const real nxx = (s13 - s24) - (jx * ux - jy * uy);  // m_pxx^eq = rho (ux^2 - uy^2)
+  const real nxy = (s57 - s68) - jx * uy;              // m_pxy^eq = rho ux uy
+  // Li source S (Eq. S): (0, 6 u.F + sigma term, -6 u.F - sigma term, Fx, -Fx, Fy, -Fy,
+  // 2 (ux Fx - uy Fy), ux Fy + uy Fx); kappa correction C (Eq. C) on e, eps, pxx, pxy
   const real uF = ux * Fx + uy * Fy;
-  const real S1 = real(6) * uF + P.sigma12_e * Fm2_over_psi2;
-  const real S2 = -real(6) * uF - P.sigma12_z * Fm2_over_psi2;
-  const real S7 = real(2) * (ux * Fx - uy * Fy);
-  const real S8 = ux * Fy + uy * Fx;
-  const real qs = Qxx + Qyy;
-  const real C1 = real(1.5) * P.s[1] * qs;
-  const real C2 = -real(1.5) * P.s[2] * qs;
-  const real C7 = -s_eta * (Qxx - Qyy);
-  const real C8 = -s_eta * Qxy;
-  // moment increments dm = -Lambda (m - m^eq) + (I - Lambda/2) S + C; dm_0 = 0 (S_0 = C_0 = 0),
-  // so f* = f + M^-1 dm leaves the mass untouched by construction (no rounding bias from
-  // the 1/9 scaling of the density row)
-  const real h = real(0.5);
-  const real d1 = -P.s[1] * n1 + (real(1) - h * P.s[1]) * S1 + C1;
-  const real d2 = -P.s[2] * n2 + (real(1) - h * P.s[2]) * S2 + C2;
-  const real d3 = -P.s[3] * n3 + (real(1) - h * P.s[3]) * Fx;
-  const real d4 = -P.s[4] * n4 - (real(1) - h * P.s[4]) * Fx;
-  const real d5 = -P.s[5] * n5 + (real(1) - h * P.s[5]) * Fy;
-  const real d6 = -P.s[6] * n6 - (real(1) - h * P.s[6]) * Fy;
-  const real d7 = -s_eta * n7 + (real(1) - h * s_eta) * S7 + C7;
-  const real d8 = -s_eta * n8 + (real(1) - h * s_eta) * S8 + C8;
-  // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-  const real a1 = d1 * (real(1) / real(36)), a2 = d2 * (real(1) / real(36));
-  const real a3 = d3 * (real(1) / real(6)), a4 = d4 * (real(1) / real(12)), a5 = d5 * (real(1) / real(6));
-  const real a6 = d6 * (real(1) / real(12)), a7 = d7 * real(0.25), a8 = d8 * real(0.25);
-  const real ca = -a1 - real(2) * a2;
-  const real cd = real(2) * a1 + a2;
-  fd[0] += -real(4) * a1 + real(4) * a2;
-  fd[1] += ca + a3 - real(2) * a4 + a7;
-  fd[2] += ca + a5 - real(2) * a6 - a7;
-  fd[3] += ca - a3 + real(2) * a4 + a7;
-  fd[4] += ca - a5 + real(2) * a6 - a7;
-  fd[5] += cd + a3 + a4 + a5 + a6 + a8;
-  fd[6] += cd - a3 - a4 + a5 + a6 - a8;
-  fd[7] += cd - a3 - a4 - a5 - a6 + a8;
-  fd[8] += cd + a3 + a4 - a5 - a6 - a8;
+  const real a1 = P.c1n * ne + P.c1q * qs + P.c1u * uF + P.c1f * fm2;
+  const real a2 = P.c2n * nz + P.c2q * qs + P.c2u * uF + P.c2f * fm2;
+  const real a3 = Fx * (real(1) / real(6)), a5 = Fy * (real(1) / real(6));
+  const real a4 = P.c4n * nqx + P.c4f * Fx;
+  const real a6 = P.c6n * nqy + P.c6f * Fy;
+  const real g = real(0.25) - real(0.5) * e;  // (1 - s_eta / 2) / 4
+  const real a7 = (g + g) * (ux * Fx - uy * Fy) - e * (nxx + qd);
+  const real a8 = g * (ux * Fy + uy * Fx) - e * (nxy + qxy);
+  // f* = f + M^T a
+  const real ca = -a1 - real(2) * a2, cd = real(2) * a1 + a2;
+  const real u4 = a3 - real(2) * a4, v6 = a5 - real(2) * a6;
+  const real cp = ca + a7, cn = ca - a7;
+  const real p34 = a3 + a4, p56 = a5 + a6;
+  const real e5 = cd + a8, e6 = cd - a8;
+  const real pp = p56 + p34, pm = p56 - p34;
+  fd[0] += real(4) * (a2 - a1);
+  fd[1] += cp + u4;
+  fd[3] += cp - u4;
+  fd[2] += cn + v6;
+  fd[4] += cn - v6;
+  fd[5] += e5 + pp;
+  fd[7] += e5 - pp;
+  fd[6] += e6 + pm;
+  fd[8] += e6 - pm;
 }
 
 template <typename real>

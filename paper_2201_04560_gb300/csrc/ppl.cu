@@ -356,6 +356,30 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
       P.kappa_G2.d = c.G / 2.0;
     }
   }
+  // collide() coefficients: a_1 = dm_1 / 36, a_2 = dm_2 / 36 (eps enters as a third of its
+  // non-equilibrium part), a_4 = dm_4 / 12, a_6 = dm_6 / 12, with dm = -s n + (1 - s/2) S + C
+  // and C_1 = 3/2 s_1 (Qxx + Qyy), C_2 = -3/2 s_2 (Qxx + Qyy) (Eqs. collisionMRT, S, C); the
+  // sigma terms are formed in real arithmetic so that a sigma tangent carries through
+  {
+    const double *s = c.s;
+    P.c1n = (real)(-s[1] / 36.0);
+    P.c1q = (real)(s[1] / 24.0);
+    P.c1u = (real)((1.0 - 0.5 * s[1]) / 6.0);
+    P.c1f = P.sigma12_e * (real)((1.0 - 0.5 * s[1]) / 36.0);
+    P.c2n = (real)(-s[2] / 12.0);
+    P.c2q = (real)(-s[2] / 24.0);
+    P.c2u = (real)(-(1.0 - 0.5 * s[2]) / 6.0);
+    P.c2f = P.sigma12_z * (real)(-(1.0 - 0.5 * s[2]) / 36.0);
+    P.c4n = (real)(-s[4] / 12.0);
+    P.c4f = (real)(-(1.0 - 0.5 * s[4]) / 12.0);
+    P.c6n = (real)(-s[6] / 12.0);
+    P.c6f = (real)(-(1.0 - 0.5 * s[6]) / 12.0);
+    // s_eta = 1 / (3 nu + 1/2) with nu linear in rho between the phases
+    const double e1 = P.var_eta ? 12.0 * (c.eta_l - c.eta_v) / (c.rho_l - c.rho_v) : 0.0;
+    P.e_c1 = (real)e1;
+    P.e_c0 = (real)(12.0 * c.eta_v + 2.0 - e1 * c.rho_v);
+    P.e_const = (real)(0.25 * s[7]);
+  }
   P.mod_psi = c.contact_model == PPL_CONTACT_MOD_PSI ? 1 : 0;
   P.Gw_over_G = (real)(c.G_w / c.G);
   P.gx = (real)c.gx;

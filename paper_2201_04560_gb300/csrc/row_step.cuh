@@ -90,16 +90,24 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename real>
 struct S3Carry {  // S2 (row r) -> S3 (row r, next iteration)
   real fmx, fmy, fm2, inv_rho;  // F^m, |F^m|^2 / psi^2 = G^2 |s|^2, 1/rho
-  real qxx, qyy, qxy;           // Q of Eq. (Q)
+  real qs, qd, qxy;             // Q of Eq. (Q) as Qxx + Qyy, Qxx - Qyy, Qxy
 };
 template <typename real>
 struct S4Carry {  // S3 (row r) -> S4 (row r, next iteration)
   real k1, lam, gdx, gdy, div, inv_rcv, ux, uy, A, B, Fx, Fy;
 };
 
+// FP64 keeps the EOS parts A, B, E of each node from the first stage for the compression
+// term of the collision stage (rings [4][NT]), where a division and a square root cost
+// more than three shared-memory round trips; the other precisions recompute them
+template <typename real>
+__host__ __device__ constexpr bool eos_ring() {
+  return std::is_same<real, double>::value;
+}
+
 template <int NT, int PF, typename real>
 constexpr size_t row_step_smem_bytes() {
-  return (size_t)((PF + 3) * 10 + 5 * 4 + 18 + 3) * NT * sizeof(real);
+  return (size_t)((PF + 3) * 10 + 5 * 4 + 18 + 3 + (eos_ring<real>() ? 12 : 0)) * NT * sizeof(real);
 }
 
 // Deterministic FP64 reduction of sum rho^{n+1} over the grid: the CTA's partial (acc of
@@ -182,6 +190,9 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
   // 7, 8), row mod 3; f*_0, f*_2, f*_4 stay in the column and are handed over in registers
   real *rfs = ruy + 4 * NT;
   real *rTs = rfs + 18 * NT;  // [3][NT] first Heun stage T*, row mod 3
+  real *rA = rTs + 3 * NT;    // [4][NT] EOS parts of the row (eos_ring), row mod 4
+  real *rB = rA + 4 * NT;
+  real *rE = rB + 4 * NT;
   const real third = real(1) / real(3), twelfth = real(1) / real(12);
   const real big = sizeof(real) == 4 ? real(3.0e38) : real(1.0e300);
 
@@ -260,12 +271,21 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
       const real delta = ((f[0] + (f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8])));
       const real rho = P.rho_ref + delta;
       real psi = real(0);
+      const int i0 = s4_0 * NT + t;
       if (!cm.solid && !rm.solid) {
-        const real arg = psi_arg(P, rho, P.T_ref + Tt);
+        real arg;
+        if constexpr (eos_ring<real>()) {
+          real A, B, E;
+          arg = psi_arg_eos(P, rho, P.T_ref + Tt, &A, &B, &E);
+          rA[i0] = A;
+          rB[i0] = B;
+          rE[i0] = E;
+        } else {
+          arg = psi_arg(P, rho, P.T_ref + Tt);
+        }
         if (!(arg >= real(0))) flags |= FLAG_PSI_NEG;
         psi = sqrt(fmax(arg, real(0)));
       }
-      const int i0 = s4_0 * NT + t;
       rpsi[i0] = psi;
       rrho[i0] = rho;
       rT[i0] = Tt;
@@ -283,14 +303,14 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
         if (!cm.solid && !rm.solid) {
           const real p1 = rpsi[i0 + 1], p3 = rpsi[i0 - 1], p2 = rpsi[iu], p4 = rpsi[id];
           const real p5 = rpsi[iu + 1], p6 = rpsi[iu - 1], p7 = rpsi[id - 1], p8 = rpsi[id + 1];
-          real sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
-          real sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
           const real psi_c = rpsi[i0];
-          // Q (Eq. Q) from the same psi neighbourhood
-          const real dsum = twelfth * (p5 + p6 + p7 + p8 - real(4) * psi_c);
-          real qxx = third * (p1 + p3 - real(2) * psi_c) + dsum;
-          real qyy = third * (p2 + p4 - real(2) * psi_c) + dsum;
-          const real qxy = twelfth * (p5 - p6 + p7 - p8);
+          const real d57 = p5 - p7, d86 = p8 - p6, s57 = p5 + p7, s68 = p6 + p8, s13 = p1 + p3, s24 = p2 + p4;
+          real sx = third * (p1 - p3) + twelfth * (d57 + d86);
+          real sy = third * (p2 - p4) + twelfth * (d57 - d86);
+          // Q (Eq. Q) from the same psi neighbourhood, as Qxx + Qyy, Qxx - Qyy and Qxy
+          real qs = third * (s13 + s24) + (real(1) / real(6)) * (s57 + s68) - real(2) * psi_c;
+          real qd = third * (s13 - s24);
+          const real qxy = twelfth * (s57 - s68);
           const int ws = cm.wall >= 0 ? cm.wall : rm.wall;
           if (ws >= 0) {
             // solid links (psi = 0 in the ring): their force weights sum to 1/2 along the
@@ -313,17 +333,13 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
             else if (ws == 1) sx += hw;
             else if (ws == 2) sy -= hw;
             else sy += hw;
-            if (ws < 2) {
-              qxx += real(0.5) * pq;
-              qyy += (real(1) / real(6)) * pq;
-            } else {
-              qxx += (real(1) / real(6)) * pq;
-              qyy += real(0.5) * pq;
-            }
+            qs += (real(2) / real(3)) * pq;
+            if (ws < 2) qd += third * pq;
+            else qd -= third * pq;
           }
           const real qf = P.kappa_G2 * psi_c;
-          n2.qxx = qf * qxx;
-          n2.qyy = qf * qyy;
+          n2.qs = qf * qs;
+          n2.qd = qf * qd;
           n2.qxy = qf * qxy;
           const real rho = rrho[i0];
           const real gps = -P.G * psi_c;
@@ -373,15 +389,12 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
           real fd[9];
 #pragma unroll
           for (int i = 0; i < 9; ++i) fd[i] = st[i * NT];
-          // the mass moment is the exact sum of the stored deviations (rho_ref + delta is
-          // rounded to the precision of rho)
-          const real delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
           const real rho = rrho[i0];
           const real ux = rux[i0], uy = ruy[i0];
           const real Fx = c2.fmx + P.gx * (rho - rho_bar), Fy = c2.fmy + P.gy * (rho - rho_bar);
-          real s_eta = P.s[7];
-          if (P.var_eta) s_eta = real(1) / (real(3) * (P.eta_v + (P.eta_l - P.eta_v) * (rho - P.rho_v) * P.inv_drho) + real(0.5));
-          collide(P, fd, rho, delta, ux, uy, Fx, Fy, c2.fm2, c2.qxx, c2.qyy, c2.qxy, s_eta);
+          real e = P.e_const;  // s_eta / 4
+          if (P.var_eta) e = real(1) / (P.e_c0 + P.e_c1 * rho);
+          collide(P, fd, rho, ux, uy, Fx, Fy, c2.fm2, c2.qs, c2.qd, c2.qxy, e);
           real *fs = rfs + f_r2 * 6 * NT + t;
           fs[0 * NT] = fd[1];
           fs[1 * NT] = fd[3];
@@ -399,7 +412,14 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
             const real T0 = rT[i0];
             nxt.ux = ux;
             nxt.uy = uy;
-            dpdT_parts(P, rho, &nxt.A, &nxt.B);
+            real E = real(0);
+            if constexpr (eos_ring<real>()) {
+              nxt.A = rA[i0];
+              nxt.B = rB[i0];
+              E = rE[i0];
+            } else {
+              pr_parts(P, rho, &nxt.A, &nxt.B);
+            }
             nxt.inv_rcv = c2.inv_rho * P.cv_inv;
             nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
             // frozen coefficients of Eq. (energy-equation): grad lambda = dlam grad rho, div u
@@ -424,8 +444,9 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
               const real gty = third * (t2 - t4) + twelfth * (t5 + t6 - t7 - t8);
               const real lap = (real(2) / real(3)) * (t1 + t2 + t3 + t4 - real(4) * T0) +
                                (real(1) / real(6)) * (t5 + t6 + t7 + t8 - real(4) * T0);
+              const real TdpdT = eos_ring<real>() ? (P.T_ref + T0) * nxt.A + E : T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0);
               const real k1 = -(ux * gtx + uy * gty) + (nxt.lam * lap + nxt.gdx * gtx + nxt.gdy * gty) * nxt.inv_rcv -
-                              T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0) * nxt.div * nxt.inv_rcv;
+                              TdpdT * nxt.div * nxt.inv_rcv;
               nxt.k1 = k1;
               Ts = T0 + k1;
             }

@@ -153,13 +153,14 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       if (!rm.solid) {
         const Trip pu = trip<SW>(rpsi + iu, t), pm = trip<SW>(rpsi + i0, t), pd = trip<SW>(rpsi + id, t);
         const F2 p1 = pm.r, p3 = pm.l, p2 = pu.c, p4 = pd.c, p5 = pu.r, p6 = pu.l, p7 = pd.l, p8 = pd.r;
-        F2 sx = third * (p1 - p3) + twelfth * (p5 - p6 - p7 + p8);
-        F2 sy = third * (p2 - p4) + twelfth * (p5 + p6 - p7 - p8);
         const F2 psi_c = pm.c;
-        const F2 dsum = twelfth * (p5 + p6 + p7 + p8 - 4.0f * psi_c);
-        F2 qxx = third * (p1 + p3 - 2.0f * psi_c) + dsum;
-        F2 qyy = third * (p2 + p4 - 2.0f * psi_c) + dsum;
-        const F2 qxy = twelfth * (p5 - p6 + p7 - p8);
+        const F2 d57 = p5 - p7, d86 = p8 - p6, s57 = p5 + p7, s68 = p6 + p8, s13 = p1 + p3, s24 = p2 + p4;
+        F2 sx = third * (p1 - p3) + twelfth * (d57 + d86);
+        F2 sy = third * (p2 - p4) + twelfth * (d57 - d86);
+        // Q as Qxx + Qyy, Qxx - Qyy and Qxy
+        F2 qs = third * (s13 + s24) + (1.0f / 6.0f) * (s57 + s68) - 2.0f * psi_c;
+        F2 qd = third * (s13 - s24);
+        const F2 qxy = twelfth * (s57 - s68);
         if (!SIMPLE && rm.wall >= 0) {
           // solid links of a y wall: see the one-column kernel (Eqs. shanchen-walls,
           // psi-based-formula, Q-psi-based, mod-psi-based-formula, Q-mod-psi-based)
@@ -178,12 +179,12 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           const F2 hw = 0.5f * pf;
           if (ws == 2) sy = sy - hw;
           else sy = sy + hw;
-          qxx = qxx + (1.0f / 6.0f) * pq;
-          qyy = qyy + 0.5f * pq;
+          qs = qs + (2.0f / 3.0f) * pq;
+          qd = qd - third * pq;
         }
         const F2 qf = P.kappa_G2 * psi_c;
-        nn2.qxx = qf * qxx;
-        nn2.qyy = qf * qyy;
+        nn2.qs = qf * qs;
+        nn2.qd = qf * qd;
         nn2.qxy = qf * qxy;
         const F2 rho = ld2(rrho + i0 + c2);
         const F2 gps = (-P.G) * psi_c;
@@ -219,13 +220,12 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         F2 fd[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fd[i] = ld2(st + i * SW);
-        const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const F2 rho = ld2(rrho + i0 + c2);
         const F2 ux = ld2(rux + i0 + c2), uy = ld2(ruy + i0 + c2);
         const F2 Fx = cc2.fmx + P.gx * (rho - rho_bar), Fy = cc2.fmy + P.gy * (rho - rho_bar);
-        F2 s_eta(P.s[7]);
-        if (P.var_eta) s_eta = 1.0f / (3.0f * (P.eta_v + (P.eta_l - P.eta_v) * ((rho - P.rho_v) * P.inv_drho)) + 0.5f);
-        collide(P, fd, rho, delta, ux, uy, Fx, Fy, cc2.fm2, cc2.qxx, cc2.qyy, cc2.qxy, s_eta);
+        F2 e(P.e_const);  // s_eta / 4
+        if (P.var_eta) e = 1.0f / (P.e_c0 + P.e_c1 * rho);
+        collide(P, fd, rho, ux, uy, Fx, Fy, cc2.fm2, cc2.qs, cc2.qd, cc2.qxy, e);
         float *fs = rfs + f_r2 * 6 * SW + c2;
         st2(fs + 0 * SW, fd[1]);
         st2(fs + 1 * SW, fd[3]);
@@ -242,7 +242,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           const F2 T0 = ld2(rT + i0 + c2);
           nxt.ux = ux;
           nxt.uy = uy;
-          dpdT_parts(P, rho, &nxt.A, &nxt.B);
+          pr_parts(P, rho, &nxt.A, &nxt.B);
           nxt.inv_rcv = cc2.inv_rho * P.cv_inv;
           nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
           const Trip ru = trip<SW>(rrho + iu, t), rmd = trip<SW>(rrho + i0, t), rd = trip<SW>(rrho + id, t);
