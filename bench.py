@@ -394,7 +394,8 @@ def main():
         dt = max_over_ranks(dt, dist, "cuda")
         n = sim.norms()
         out[prec] = {"dt": dt, "steps": steps, "launches": launches, "clocks": clocks, "flags": n["flags"],
-                     "mass": n["mass"], "kernel": sim.kernel, "rows_per_cta": sim.launch()[0]}
+                     "mass": n["mass"], "kernel": sim.kernel, "rows_per_cta": sim.launch()[0],
+                     "staging": "tma" if sim.tma_staging else "cp.async"}
         if prec == "fp32" and not args.no_e2e:
             # end to end through the C ABI: pinned host inputs -> device, K steps, fields -> host
             host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory() for a in ic]
@@ -443,7 +444,8 @@ def main():
                    "grid": [NX, NY], "l2": "state (335 MB FP32, 671 MB FP64 per buffer) larger than L2",
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "kernel": {"fp32": f32["kernel"], "fp64": f64["kernel"]},
-                   "rows_per_cta": {"fp32": f32["rows_per_cta"], "fp64": f64["rows_per_cta"]}},
+                   "rows_per_cta": {"fp32": f32["rows_per_cta"], "fp64": f64["rows_per_cta"]},
+                   "fp32_row_staging": f32["staging"]},
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                      "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,

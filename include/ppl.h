@@ -78,6 +78,8 @@ extern "C" {
 #define PPL_FLAG_PSI_NEG 1u /* 2 (p_EOS - rho/3) / G < 0 somewhere: psi undefined */
 #define PPL_FLAG_NAN 2u     /* NaN or Inf in rho or T */
 #define PPL_FLAG_RHO_NONPOS 4u
+#define PPL_FLAG_STALL 8u   /* a staged row copy did not land within the step kernel's wait limit:
+                               that step's result is invalid */
 
 /*
  * Simulation configuration (Sec. 2 model parameters; Sec. 3 scaling is applied by the caller).
@@ -382,6 +384,10 @@ int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
 int ppl_select_kernel(ppl_t *h, int kernel);
 int ppl_get_kernel(const ppl_t *h);
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
+/* 1 if the two-column FP32 step stages rows by TMA (tensor maps of the state were encoded at
+ * ppl_init: FP32, nx a multiple of 4 and at least one strip wide), 0 if every strip uses
+ * per-thread row copies; strips that wrap across the periodic x seam always use the latter. */
+int ppl_tma_staging(const ppl_t *h);
 
 /* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256), for
  * each applicable step kernel (ppl_select_kernel), with CUDA events on the handle's

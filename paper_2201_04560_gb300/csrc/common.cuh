@@ -19,7 +19,7 @@ namespace ppl_dev {
 
 enum { PERIODIC = 0, WALL = 1, OUTFLOW = 2 };
 enum { T_PERIODIC = 0, T_DIRICHLET = 1, T_ADIABATIC = 2 };
-enum : unsigned { FLAG_PSI_NEG = 1u, FLAG_NAN = 2u, FLAG_RHO_NONPOS = 4u };
+enum : unsigned { FLAG_PSI_NEG = 1u, FLAG_NAN = 2u, FLAG_RHO_NONPOS = 4u, FLAG_STALL = 8u };
 
 template <typename real>
 struct Params {
@@ -63,6 +63,10 @@ struct StepIO {
   double *partials;        // one FP64 partial per CTA (two for the tangent step)
   unsigned *counter;       // CTAs done (reset by the last one)
   unsigned *status;        // PPL_FLAG_* bits
+  // TMA descriptors (CUtensorMap, global memory) of f_in as [9][ny][nx] and T_in as [ny][nx]
+  // with a box of one row of the FP32 two-column strip, or null (per-thread row copies)
+  const void *tmap_f;
+  const void *tmap_T;
 };
 
 // lattice of Sec. 2
@@ -82,8 +86,9 @@ __device__ __forceinline__ real wgt(int i) {
 // E = -T alpha'(T) B = k B alpha^(1/2) sqrt(T/Tc).
 template <typename PT, typename real>
 __device__ __forceinline__ void pr_parts(const Params<PT> &P, real rho, real *A, real *B) {
-  const real omb = real(1) - P.b * rho;
-  const real den = real(1) + real(2) * P.b * rho - P.b * P.b * rho * rho;
+  const PT nb = -P.b, twob = P.b + P.b, nbb = -(P.b * P.b);
+  const real omb = rho * nb + real(1);
+  const real den = rho * (rho * nbb + twob) + real(1);  // 1 + 2 b rho - b^2 rho^2
   const real inv = real(1) / (omb * den);  // one division for both parts
   *A = rho * P.R * den * inv;
   *B = P.a * rho * rho * omb * inv;
@@ -95,8 +100,8 @@ __device__ __forceinline__ real psi_arg_eos(const Params<PT> &P, real rho, real 
   const real ar = real(1) + P.k * (real(1) - st);
   pr_parts(P, rho, A, B);
   *E = P.k * *B * ar * st;
-  const real p = T * *A - ar * ar * *B;
-  return (p - rho * (real(1) / real(3))) * P.twoG_inv;
+  const real TA = T * *A, ar2B = ar * ar * *B;
+  return ((TA - (real(1) / real(3)) * rho) - ar2B) * P.twoG_inv;  // (p - rho/3) 2/G
 }
 template <typename PT, typename real>
 __device__ __forceinline__ real psi_arg(const Params<PT> &P, real rho, real T) {
@@ -281,36 +286,40 @@ __device__ __forceinline__ void collide(const Params<PT> &P, real fd[9], real rh
   const real s68 = fd[6] + fd[8], d68 = fd[6] - fd[8];
   const real ax = s13 + s24, dg = s57 + s68;
   const real jx = rho * ux, jy = rho * uy;  // rho u = m_j + F/2
-  const real ru2 = jx * ux + jy * uy;
+  const real y2 = jy * uy;
+  const real ru2 = jx * ux + y2;  // rho u^2
   const real ne = real(4) * dg + (ax - real(2) * fd[0]) - real(3) * ru2;  // m_e - m_e^eq
   const real nz = (fd[0] - ax) + ru2;                                     // (m_eps - m_eps^eq) / 3
   const real nqx = ((d57 - d68) - real(2) * d13) + jx;                    // m_qx^eq = -rho ux
   const real nqy = ((d57 + d68) - real(2) * d24) + jy;
-  const real nxx = (s13 - s24) - (jx * ux - jy * uy);  // m_pxx^eq = rho (ux^2 - uy^2)
-  const real nxy = (s57 - s68) - jx * uy;              // m_pxy^eq = rho ux uy
+  // pxx, pxy enter with -s_eta: their non-equilibrium parts are formed negated
+  const real mxx = (ru2 - real(2) * y2) - (s13 - s24);  // m_pxx^eq - m_pxx, m_pxx^eq = rho (ux^2 - uy^2)
+  const real mxy = jx * uy + (s68 - s57);               // m_pxy^eq - m_pxy, m_pxy^eq = rho ux uy
   // Li source S (Eq. S): (0, 6 u.F + sigma term, -6 u.F - sigma term, Fx, -Fx, Fy, -Fy,
   // 2 (ux Fx - uy Fy), ux Fy + uy Fx); kappa correction C (Eq. C) on e, eps, pxx, pxy
-  const real uF = ux * Fx + uy * Fy;
+  const real yF = uy * Fy;
+  const real uF = ux * Fx + yF;
   const real a1 = P.c1n * ne + P.c1q * qs + P.c1u * uF + P.c1f * fm2;
   const real a2 = P.c2n * nz + P.c2q * qs + P.c2u * uF + P.c2f * fm2;
   const real a3 = Fx * (real(1) / real(6)), a5 = Fy * (real(1) / real(6));
   const real a4 = P.c4n * nqx + P.c4f * Fx;
   const real a6 = P.c6n * nqy + P.c6f * Fy;
   const real g = real(0.25) - real(0.5) * e;  // (1 - s_eta / 2) / 4
-  const real a7 = (g + g) * (ux * Fx - uy * Fy) - e * (nxx + qd);
-  const real a8 = g * (ux * Fy + uy * Fx) - e * (nxy + qxy);
-  // f* = f + M^T a
-  const real ca = -a1 - real(2) * a2, cd = real(2) * a1 + a2;
+  const real a7 = e * (mxx - qd) + (g + g) * (uF - real(2) * yF);
+  const real a8 = e * (mxy - qxy) + g * (ux * Fy + uy * Fx);
+  // f* = f + M^T a: f1, f3 get a7 - (a1 + 2 a2) +- (a3 - 2 a4); f2, f4 get -(a1 + 2 a2 + a7) +-
+  // (a5 - 2 a6); the diagonals get 2 a1 + a2 +- a8 +- (a3 + a4) +- (a5 + a6)
+  const real b1 = a1 + real(2) * a2, cd = real(2) * a1 + a2;
   const real u4 = a3 - real(2) * a4, v6 = a5 - real(2) * a6;
-  const real cp = ca + a7, cn = ca - a7;
+  const real cp = a7 - b1, cn = b1 + a7;
   const real p34 = a3 + a4, p56 = a5 + a6;
   const real e5 = cd + a8, e6 = cd - a8;
   const real pp = p56 + p34, pm = p56 - p34;
   fd[0] += real(4) * (a2 - a1);
   fd[1] += cp + u4;
   fd[3] += cp - u4;
-  fd[2] += cn + v6;
-  fd[4] += cn - v6;
+  fd[2] += v6 - cn;
+  fd[4] -= cn + v6;
   fd[5] += e5 + pp;
   fd[7] += e5 - pp;
   fd[6] += e6 + pm;

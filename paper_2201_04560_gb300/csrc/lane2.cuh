@@ -1,9 +1,11 @@
 // Two FP32 lanes (two adjacent columns of the row-marching step) computed with the packed
 // f32x2 instructions of sm_100+ (one FMA/ADD/MUL instruction for both lanes).
 //
-// Products are kept pending (Mul2) so that a product followed by an addition or
-// subtraction becomes one fused multiply-add, as the compiler contracts the scalar code.
-// Division and square root act lane by lane.
+// Products are kept pending (Mul2) so that a product followed by an addition becomes one
+// fused multiply-add, as the compiler contracts the scalar code. The packed instructions
+// take no negated operand, so a difference is one packed subtraction (sub.rn.f32x2, written
+// out below) and a product is subtracted after rounding unless its first factor is a
+// constant that the compiler negates. Division and square root act lane by lane.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,6 +30,15 @@ struct Mul2 {  // a * b, not yet rounded
 };
 
 __device__ __forceinline__ float2 neg2(float2 x) { return make_float2(-x.x, -x.y); }
+// a - b in one packed instruction (PTX sub.f32x2, sm_100+)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 __device__ __forceinline__ F2 ev(F2 x) { return x; }
 __device__ __forceinline__ F2 ev(Mul2 m) { return F2(__fmul2_rn(m.a, m.b)); }
 
@@ -51,12 +62,12 @@ __device__ __forceinline__ F2 operator+(float s, F2 a) { return a + F2(s); }
 __device__ __forceinline__ F2 operator+(Mul2 m, float s) { return m + F2(s); }
 __device__ __forceinline__ F2 operator+(float s, Mul2 m) { return m + F2(s); }
 
-__device__ __forceinline__ F2 operator-(F2 a) { return F2(neg2(a.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(sub2(make_float2(0.0f, 0.0f), a.v)); }
 __device__ __forceinline__ Mul2 operator-(Mul2 m) { return Mul2{neg2(m.a), m.b}; }
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, neg2(b.v))); }
-__device__ __forceinline__ F2 operator-(Mul2 m, F2 c) { return F2(__ffma2_rn(m.a, m.b, neg2(c.v))); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(sub2(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(Mul2 m, F2 c) { return F2(sub2(ev(m).v, c.v)); }
 __device__ __forceinline__ F2 operator-(F2 c, Mul2 m) { return F2(__ffma2_rn(neg2(m.a), m.b, c.v)); }
-__device__ __forceinline__ F2 operator-(Mul2 m, Mul2 n) { return F2(__ffma2_rn(m.a, m.b, neg2(ev(n).v))); }
+__device__ __forceinline__ F2 operator-(Mul2 m, Mul2 n) { return F2(sub2(ev(m).v, ev(n).v)); }
 __device__ __forceinline__ F2 operator-(F2 a, float s) { return a - F2(s); }
 __device__ __forceinline__ F2 operator-(float s, F2 a) { return F2(s) - a; }
 __device__ __forceinline__ F2 operator-(Mul2 m, float s) { return m - F2(s); }

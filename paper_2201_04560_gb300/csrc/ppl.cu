@@ -5,6 +5,7 @@
 // instantiated in step_fp32.cu, step_fp64.cu and step_tangent.cu. The refinement tools
 // built on it are in tools.cu.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled: the encoder is taken from the driver at run time
 
 #include <algorithm>
 #include <cmath>
@@ -418,6 +419,8 @@ int launch_step_t(ppl_sim *h, bool energy) {
   io.partials = h->partials;
   io.counter = h->counter;
   io.status = h->status;
+  io.tmap_f = h->tmaps ? (const unsigned char *)h->tmaps + h->cur * sizeof(CUtensorMap) : nullptr;
+  io.tmap_T = h->tmaps ? (const unsigned char *)h->tmaps + (2 + h->cur) * sizeof(CUtensorMap) : nullptr;
   int H = h->rows_per_cta;
   void *args[] = {(void *)&P, (void *)&io, (void *)&H};
   CK(cudaLaunchKernel(h->var.fn[energy ? 1 : 0], h->grid, dim3(h->var.nt), args, h->var.smem, h->stream));
@@ -425,6 +428,46 @@ int launch_step_t(ppl_sim *h, bool energy) {
   h->step += 1;
   h->launches += 1;
   return PPL_OK;
+}
+
+// Tensor maps of the FP32 state for the TMA row staging of the two-column step: f as
+// [9][ny][nx] with a box of one row of the 2 kNTP-column strip over all nine planes, T as
+// [ny][nx] with a box of one row; one pair per ping-pong buffer, in device memory. Left
+// unset (the step then stages rows with per-thread copies) where the driver offers no
+// encoder, the row pitch is not a multiple of 16 bytes (nx % 4 != 0) or no strip fits.
+void build_tensor_maps(ppl_sim *h) {
+  h->tmaps = nullptr;
+  const int box = 2 * kNTP;
+  if (h->prec != PPL_FP32DEV || h->nx % 4 != 0 || h->nx < box) return;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return;
+  const auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  CUtensorMap maps[4];
+  const cuuint64_t nx = (cuuint64_t)h->nx, ny = (cuuint64_t)h->ny;
+  const cuuint32_t unit[3] = {1, 1, 1};
+  for (int b = 0; b < 2; ++b) {
+    const cuuint64_t fdim[3] = {nx, ny, 9}, fstride[2] = {nx * 4, nx * ny * 4};
+    const cuuint32_t fbox[3] = {(cuuint32_t)box, 1, 9};
+    const cuuint64_t tdim[2] = {nx, ny}, tstride[1] = {nx * 4};
+    const cuuint32_t tbox[2] = {(cuuint32_t)box, 1};
+    if (encode(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[b], fdim, fstride, fbox, unit,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&maps[2 + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->T[b], tdim, tstride, tbox, unit,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return;
+  }
+  void *d = nullptr;
+  if (cudaMalloc(&d, sizeof(maps)) != cudaSuccess) return;
+  if (cudaMemcpy(d, maps, sizeof(maps), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return;
+  }
+  h->tmaps = d;
 }
 
 int launch_step(ppl_sim *h, bool energy) {
@@ -547,6 +590,7 @@ void free_all(ppl_sim *h) {
     cudaFree(h->stats[i]);
   }
   cudaFree(h->bnd);
+  cudaFree(h->tmaps);
   cudaFree(h->partials);
   cudaFree(h->norm_out);
   cudaFree(h->counter);
@@ -714,6 +758,7 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
       cudaMalloc(&h->upload, (size_t)4 * h->N * sizeof(double)) != cudaSuccess)
     return fail(PPL_E_NOMEM);
   if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned), h->stream) != cudaSuccess) return fail(PPL_E_CUDA);
+  build_tensor_maps(h);
 
   // boundary arrays in the working precision
   size_t bbytes = 0;
@@ -1061,6 +1106,8 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   io.partials = scratch;
   io.counter = counter;
   io.status = status;
+  io.tmap_f = nullptr;  // caller-owned buffers: per-thread row copies
+  io.tmap_T = nullptr;
   const int e = cfg->energy_on ? 1 : 0;
   if (cfg->precision == PPL_FP64) {
     Params<double> P;

@@ -27,6 +27,7 @@ struct ppl_sim {
   void *f[2] = {nullptr, nullptr};
   void *T[2] = {nullptr, nullptr};
   void *bnd = nullptr;  // device copies of the per-node boundary arrays
+  void *tmaps = nullptr;  // FP32: 4 CUtensorMap (f[0], f[1], T[0], T[1]) for the TMA row staging, or null
   double *stats[2] = {nullptr, nullptr};
   double *partials = nullptr;  // max(#step CTAs (x2 for tangents), kStats * #stats blocks)
   size_t npart = 0;            // doubles in partials

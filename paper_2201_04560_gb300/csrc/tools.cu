@@ -400,6 +400,11 @@ int ppl_get_kernel(const ppl_t *h) {
   return h->var.fn[0] == step_variant_fp32_pair().fn[0] ? PPL_KERNEL_PAIR : PPL_KERNEL_COLUMN;
 }
 
+int ppl_tma_staging(const ppl_t *h) {
+  if (!h) return PPL_E_INVAL;
+  return h->tmaps ? 1 : 0;
+}
+
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas) {
   if (!h) return PPL_E_INVAL;
   if (rows_per_cta) *rows_per_cta = h->rows_per_cta;

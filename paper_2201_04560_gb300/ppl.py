@@ -129,6 +129,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_select_kernel.restype = ctypes.c_int
     L.ppl_get_kernel.argtypes = [H]
     L.ppl_get_kernel.restype = ctypes.c_int
+    L.ppl_tma_staging.argtypes = [H]
+    L.ppl_tma_staging.restype = ctypes.c_int
     L.ppl_phase_area.argtypes = [H, _D, _D, _PD]
     L.ppl_relative_change.argtypes = [_PD, _PD, ctypes.c_int64, _PD]
     L.ppl_wall_heat_flux.argtypes = [H, ctypes.c_int, _PD]
@@ -359,6 +361,11 @@ class Simulation:
     @property
     def kernel(self) -> str:
         return {1: "column", 2: "pair"}[int(self.lib.ppl_get_kernel(self.h))]
+
+    @property
+    def tma_staging(self) -> bool:
+        """The two-column FP32 step stages rows by TMA (strips off the periodic x seam)."""
+        return bool(self.lib.ppl_tma_staging(self.h))
 
     def launch(self):
         """(rows per CTA, CTAs per step launch)."""

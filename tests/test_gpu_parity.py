@@ -206,7 +206,7 @@ def test_sessile_droplet_contact_models_fp64(sim_cls, th, model, axis):
     assert_fp64_parity(got, want)
 
 
-@pytest.mark.parametrize("case", ["pool", "droplet", "ragged"])
+@pytest.mark.parametrize("case", ["pool", "droplet", "ragged", "pool_tma"])
 def test_pair_kernel_fp32_against_oracle_and_column_kernel(sim_cls, th, case):
     # the two-column FP32 kernel (packed f32x2) is chosen automatically for x-periodic
     # domains with even nx; it meets the FP32 budget against the FP64 oracle and agrees
@@ -220,6 +220,12 @@ def test_pair_kernel_fp32_against_oracle_and_column_kernel(sim_cls, th, case):
         rv, rl, _ = th[0.8]
         cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=64, R0=16.0, precision="fp32", kappa=0.3)
         steps = 400
+    elif case == "pool_tma":
+        # nx a multiple of 4: the three inner strips stage rows by TMA, the two strips on the
+        # periodic seam by per-thread copies
+        rv, rl, _ = th[0.86]
+        cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=488, ny=61, g=3e-5, precision="fp32")
+        steps = 300
     else:
         rv, rl, _ = th[0.8]
         cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=246, ny=45, R0=14.0, precision="fp32")
@@ -228,6 +234,7 @@ def test_pair_kernel_fp32_against_oracle_and_column_kernel(sim_cls, th, case):
         steps = 200
     pair = sim_cls(cfg, *ic)
     assert pair.kernel == "pair"
+    assert pair.tma_staging == (cfg["nx"] % 4 == 0 and cfg["nx"] >= 128)
     pair.step(steps)
     got = pair.fields()
     col = sim_cls(cfg, *ic)
