@@ -389,6 +389,12 @@ int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
  * per-thread row copies; strips that wrap across the periodic x seam always use the latter. */
 int ppl_tma_staging(const ppl_t *h);
 
+/* Check of the step kernel's bounded waits: launches one CTA on the current device that waits,
+ * with the wait used for TMA-staged rows, on an mbarrier that nothing completes, for limit_ns
+ * (1 .. 1e9), and stores the status word it leaves in *flags (PPL_FLAG_STALL expected). The
+ * context stays usable. Synchronous; PPL_E_INVAL for a limit out of range or a NULL flags. */
+int ppl_stall_probe(int64_t limit_ns, uint32_t *flags);
+
 /* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256), for
  * each applicable step kernel (ppl_select_kernel), with CUDA events on the handle's
  * stream, keeps the fastest pair, and restores the state, step

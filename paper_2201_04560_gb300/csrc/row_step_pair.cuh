@@ -54,8 +54,9 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void tmap_acquire(const void *m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(m) : "memory");
 }
-// waits for the phase of the given parity to complete; false after one second
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// waits for the phase of the given parity to complete; false after limit_ns (and at most 2^26
+// polls), so that a copy that never lands cannot hang the kernel
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns = 1000000000ull) {
   unsigned long long t0 = 0;
   for (int i = 0; i < (1 << 26); ++i) {
     unsigned ok;
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     unsigned long long now;
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(now));
     if (i == 0) t0 = now;
-    else if (now - t0 > 1000000000ull) return false;
+    else if (now - t0 > limit_ns) return false;
   }
   return false;
 }

@@ -36,4 +36,24 @@ StepVariant step_variant_fp32_pair() {
   return v;
 }
 
+// Wait-limit probe: one CTA waits, through the bounded mbarrier wait of the TMA row staging,
+// on an mbarrier that nothing arrives at; the wait runs out after limit_ns and the CTA reports
+// FLAG_STALL in the status word, as the step kernel does for a row that never lands.
+__global__ void stall_probe(unsigned long long limit_ns, unsigned *status) {
+  __shared__ unsigned long long bar;
+  const unsigned b = (unsigned)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool landed = mbar_wait(b, 0, limit_ns);
+  if (__syncthreads_or(!landed) && threadIdx.x == 0) atomicOr(status, FLAG_STALL);
+}
+
+cudaError_t launch_stall_probe(unsigned long long limit_ns, unsigned *status) {
+  stall_probe<<<1, 64>>>(limit_ns, status);
+  return cudaGetLastError();
+}
+
 }  // namespace ppl_dev

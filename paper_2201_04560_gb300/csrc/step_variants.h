@@ -3,6 +3,8 @@
 
 #include <cstddef>
 
+#include <cuda_runtime.h>
+
 namespace ppl_dev {
 
 constexpr int kNT32 = 128;  // threads (columns incl. the 3 + 3 halo) per CTA, FP32
@@ -28,5 +30,8 @@ StepVariant step_variant_fp32_pair();  // two columns per thread: hydrodynamical
 StepVariant step_variant_fp64();
 StepVariant step_variant_tangent();    // FP64 value + derivative (Dual)
 StepVariant step_variant_tangent32();  // FP32 value + derivative (DualF)
+
+// one CTA waiting on an mbarrier that nothing completes, with the step's bounded wait
+cudaError_t launch_stall_probe(unsigned long long limit_ns, unsigned *status);
 
 }  // namespace ppl_dev

@@ -400,6 +400,20 @@ int ppl_get_kernel(const ppl_t *h) {
   return h->var.fn[0] == step_variant_fp32_pair().fn[0] ? PPL_KERNEL_PAIR : PPL_KERNEL_COLUMN;
 }
 
+int ppl_stall_probe(int64_t limit_ns, uint32_t *flags) {
+  if (limit_ns <= 0 || limit_ns > 1000000000LL || !flags) return PPL_E_INVAL;
+  unsigned *d = nullptr;
+  CK(cudaMalloc(&d, sizeof(unsigned)));
+  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = launch_stall_probe((unsigned long long)limit_ns, d);
+  unsigned st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  CK(e);
+  *flags = st;
+  return PPL_OK;
+}
+
 int ppl_tma_staging(const ppl_t *h) {
   if (!h) return PPL_E_INVAL;
   return h->tmaps ? 1 : 0;

@@ -19,7 +19,7 @@ PPL_FP64_DSIGMA, PPL_FP64_DKAPPA = 2, 3  # FP64 state + its derivative w.r.t. si
 PPL_FP32_DSIGMA, PPL_FP32_DKAPPA = 4, 5  # the same in FP32 arithmetic and deviation storage
 PRECISIONS = {"fp64": PPL_FP64, "fp32": PPL_FP32DEV, "fp64_dsigma": PPL_FP64_DSIGMA,
               "fp64_dkappa": PPL_FP64_DKAPPA, "fp32_dsigma": PPL_FP32_DSIGMA, "fp32_dkappa": PPL_FP32_DKAPPA}
-FLAG_PSI_NEG, FLAG_NAN, FLAG_RHO_NONPOS = 1, 2, 4
+FLAG_PSI_NEG, FLAG_NAN, FLAG_RHO_NONPOS, FLAG_STALL = 1, 2, 4, 8
 
 _D = ctypes.c_double
 _PD = ctypes.POINTER(ctypes.c_double)
@@ -131,6 +131,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_get_kernel.restype = ctypes.c_int
     L.ppl_tma_staging.argtypes = [H]
     L.ppl_tma_staging.restype = ctypes.c_int
+    L.ppl_stall_probe.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32)]
+    L.ppl_stall_probe.restype = ctypes.c_int
     L.ppl_phase_area.argtypes = [H, _D, _D, _PD]
     L.ppl_relative_change.argtypes = [_PD, _PD, ctypes.c_int64, _PD]
     L.ppl_wall_heat_flux.argtypes = [H, ctypes.c_int, _PD]
@@ -172,6 +174,14 @@ def pressure(a, b, R, omega, T, rho):
     p, dp = _D(), _D()
     _check(load_library().ppl_pressure(a, b, R, omega, T, rho, ctypes.byref(p), ctypes.byref(dp)), "ppl_pressure")
     return p.value, dp.value
+
+
+def stall_probe(limit_ns: int) -> int:
+    """Status word left by one CTA waiting, with the step kernel's bounded mbarrier wait, on an
+    mbarrier that nothing completes (ppl_stall_probe): FLAG_STALL after limit_ns."""
+    flags = ctypes.c_uint32(0)
+    _check(load_library().ppl_stall_probe(int(limit_ns), ctypes.byref(flags)), "ppl_stall_probe")
+    return int(flags.value)
 
 
 def refine_a(a_base: float, n_base: int, n: int) -> float:

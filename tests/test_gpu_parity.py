@@ -253,6 +253,23 @@ def test_pair_kernel_fp32_against_oracle_and_column_kernel(sim_cls, th, case):
     np.testing.assert_allclose(got["ux"], ref["ux"], rtol=0, atol=1e-5)
 
 
+def test_bounded_wait_reports_stall(sim_cls, th):
+    # the TMA staging's mbarrier wait gives up after its limit: one CTA waiting on an mbarrier
+    # that nothing completes returns FLAG_STALL within the limit, and the context stays usable
+    import time
+    from paper_2201_04560_gb300 import ppl as P
+    t0 = time.perf_counter()
+    flags = P.stall_probe(2_000_000)  # 2 ms
+    assert flags == P.FLAG_STALL
+    assert time.perf_counter() - t0 < 5.0
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=40, R0=10.0, precision="fp32")
+    with sim_cls(cfg, *ic) as s:
+        s.step(10)
+        assert s.norms()["flags"] == 0
+
+
 def test_pair_kernel_selection_rules(sim_cls, th):
     e = th["e"]
     rv, rl, _ = th[0.8]
