@@ -57,6 +57,12 @@ def test_invalid_arguments_rejected_without_gpu(lib):
                            ctypes.byref(ps)) == ppl.PPL_E_INVAL
     h = ctypes.c_void_p()
     assert lib.ppl_init(None, None, None, None, None, ctypes.byref(h)) == ppl.PPL_E_INVAL
+    # the wait-limit probe checks its limit (1 ns .. 1 s) and output before touching the device
+    flags = ctypes.c_uint32(0)
+    assert lib.ppl_stall_probe(0, ctypes.byref(flags)) == ppl.PPL_E_INVAL
+    assert lib.ppl_stall_probe(2_000_000_000, ctypes.byref(flags)) == ppl.PPL_E_INVAL
+    assert lib.ppl_stall_probe(1000, None) == ppl.PPL_E_INVAL
+    assert lib.ppl_tma_staging(None) == ppl.PPL_E_INVAL
 
 
 def test_config_validation_rejects_bad_boundaries(lib):
