@@ -56,7 +56,19 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
+    def snapshot(self):
+        """One query, taken right before and right after the timed region, so that a timed
+        region shorter than the sampling period still carries a clock record."""
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            if r.returncode == 0 and r.stdout.strip():
+                self.lines.append(r.stdout.strip().splitlines()[0])
+        except (OSError, subprocess.TimeoutExpired):
+            pass
+
     def start(self):
+        self.snapshot()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
@@ -71,13 +83,15 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
-        if not self.proc:
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.snapshot()
+        if not self.lines:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -93,7 +107,9 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "sampling": "nvidia-smi every 100 ms during the timed region, plus one query right before "
+                            "and one right after it"}
 
 
 def profile_record(name, key):
@@ -147,6 +163,31 @@ def time_device(sim, steps, warmup, torch):
     return start.elapsed_time(end) / 1e3, sim.launch_count - l0
 
 
+def host_cpu():
+    """Model name and logical core count of the host that runs the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "arch": platform.machine()}
+
+
 def cpu_oracle_sample(steps=3):
     """The FP64 C oracle, single-threaded, on the same workload for a few steps."""
     from oracle import oracle
@@ -156,7 +197,8 @@ def cpu_oracle_sample(steps=3):
     o.step(steps)
     dt = time.perf_counter() - t0
     return {"value": NX * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%dx%d pool boiling, %d FP64 steps, single-threaded C oracle" % (NX, NY, steps)}
+            "sample": "%dx%d pool boiling, %d FP64 steps, single-threaded C oracle" % (NX, NY, steps),
+            **host_cpu()}
 
 
 def fp64_roofline(mlups64, ach_gbs, hbm, peaks, torch):
@@ -196,7 +238,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "pool boiling %dx%d, FP32 populations as f - w rho_ref" % (NX, NY), "grid": [NX, NY],
                    "sample": "%dx%d crop per step" % (nx, ny)},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample, **host_cpu()},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

@@ -215,8 +215,14 @@ void ppl_destroy(ppl_t *h);
  *             this step (iso_steps is not used). Per-boundary-node arrays (rho_w, T_w,
  *             T_dirichlet) are not supported here: they would need device copies.
  *  f_in, T_in    device state in: populations [9][ny][nx] and T [ny][nx], doubles for
- *             PPL_FP64, floats holding f_i - w_i rho_ref and T - T_ref for PPL_FP32DEV
- *  f_out, T_out  device state out, same layout; must not alias the inputs
+ *             PPL_FP64, floats holding f_i - w_i rho_ref and T - T_ref for PPL_FP32DEV;
+ *             each pointer 8-byte aligned
+ *  f_out, T_out  device state out, same layout and alignment; neither may overlap any
+ *             other of the four buffers (the step reads the neighbours of what it writes).
+ *             A line on an OUTFLOW side (x = nx-1 or x = 0, y likewise) is never written:
+ *             the step treats it as a copy of the first interior line and reads that line
+ *             instead, so the caller's outflow line keeps whatever it held before the call.
+ *             A caller that needs it copies the first interior line there.
  *  stats_in   device double[1]: rho_bar (mean density) of the input state
  *  stats_out  device double[2]: rho_bar and total mass of the output state
  *  status     device uint32: PPL_FLAG_* bits are OR-ed in (the caller clears it)
@@ -226,14 +232,17 @@ void ppl_destroy(ppl_t *h);
  * in a static device array of the library (4096 partials, 32 KB), held by every GPU that
  * loads the library until the process exits. A launch grid of more than 4096 CTAs (the
  * default shape is one wave of resident CTAs, so only very wide grids, beyond about 4096
- * column strips of 120-122 columns, reach it) is rejected with PPL_E_INVAL before anything
- * runs; so are the sensitivity precisions. The first call on each device
- * resolves the scratch's device address and sets kernel attributes; make that first call
- * before any stream capture. All calls share the one scratch array and it keeps the last
+ * column strips of 120-122 columns, reach it) is rejected with PPL_E_NOMEM before anything
+ * runs (the configuration is checked before the buffer pointers); the sensitivity
+ * precisions, null, misaligned or overlapping buffers with PPL_E_INVAL.
+ * The first call on each device resolves the scratch's device address and sets kernel
+ * attributes; make that first call before any stream capture. That set-up is kept for the
+ * life of the process: after cudaDeviceReset on a device the library must not be called
+ * on that device again (the resolved address would be stale). All calls share the one scratch array and it keeps the last
  * call's contents (the counter is cleared by each call): calls that overlap on the GPU,
  * on different streams or threads, race and must be serialised by the caller.
- * Returns PPL_OK, PPL_E_INVAL (bad arguments, unsupported per-node arrays, too large a
- * grid) or PPL_E_CUDA.
+ * Returns PPL_OK, PPL_E_INVAL (bad arguments, unsupported per-node arrays), PPL_E_NOMEM
+ * (a grid beyond the static scratch) or PPL_E_CUDA.
  */
 int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, void *f_out, void *T_out,
                      const double *stats_in, double *stats_out, uint32_t *status, void *cuda_stream);

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -108,11 +109,17 @@ __global__ void stats_partials(const Params<real> P, const real *f, const real *
 }
 
 // fixed-order finalize of the partials: out = {sum rho, sum|rho|, sum|T|, min/max rho, min/max T};
-// stats[0] = rho_bar, stats[1] = mass, stats[2] = d rho_bar (tangent states, else 0)
-__global__ void stats_finalize(const double *part, int nblk, double inv_nodes, double *out, double *stats) {
-  if (threadIdx.x != 0) return;
+// stats[0] = rho_bar, stats[1] = mass, stats[2] = d rho_bar (tangent states, else 0).
+// One block of kFinNT threads: thread j folds the partials j, j + kFinNT, ... in that order,
+// then the block combines the threads by a fixed shared-memory tree (the same order on every
+// run: the result is bitwise reproducible).
+constexpr int kFinNT = 256;
+__global__ void __launch_bounds__(kFinNT) stats_finalize(const double *part, int nblk, double inv_nodes, double *out,
+                                                         double *stats) {
+  __shared__ double red[kStats][kFinNT];
+  const int j = threadIdx.x;
   double s[kStats] = {0.0, 0.0, 0.0, 1e300, -1e300, 1e300, -1e300, 0.0};
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = j; b < nblk; b += kFinNT) {
     const double *p = part + (long long)b * kStats;
     s[0] += p[0];
     s[1] += p[1];
@@ -123,11 +130,25 @@ __global__ void stats_finalize(const double *part, int nblk, double inv_nodes, d
     s[6] = fmax(s[6], p[6]);
     s[7] += p[7];
   }
-  for (int j = 0; j < 7; ++j) out[j] = s[j];
-  if (stats) {
-    stats[0] = s[0] * inv_nodes;
-    stats[1] = s[0];
-    stats[2] = s[7] * inv_nodes;
+  for (int k = 0; k < kStats; ++k) red[k][j] = s[k];
+  __syncthreads();
+  for (int h = kFinNT / 2; h > 0; h >>= 1) {
+    if (j < h) {
+      double *r = &red[0][0];
+      for (int k = 0; k < kStats; ++k) {
+        const double a = r[k * kFinNT + j], c = r[k * kFinNT + j + h];
+        r[k * kFinNT + j] = (k == 3 || k == 5) ? fmin(a, c) : (k == 4 || k == 6) ? fmax(a, c) : a + c;
+      }
+    }
+    __syncthreads();
+  }
+  if (j == 0) {
+    for (int k = 0; k < 7; ++k) out[k] = red[k][0];
+    if (stats) {
+      stats[0] = red[0][0] * inv_nodes;
+      stats[1] = red[0][0];
+      stats[2] = red[7][0] * inv_nodes;
+    }
   }
 }
 
@@ -510,7 +531,7 @@ int run_stats(ppl_sim *h, double *stats_dst) {
                                                                (const real *)h->T[h->cur], h->partials,
                                                                h->status);
   CK(cudaGetLastError());
-  stats_finalize<<<1, 32, 0, h->stream>>>(h->partials, h->stats_blocks, P.inv_nodes, h->norm_out, stats_dst);
+  stats_finalize<<<1, kFinNT, 0, h->stream>>>(h->partials, h->stats_blocks, P.inv_nodes, h->norm_out, stats_dst);
   CK(cudaGetLastError());
   return PPL_OK;
 }
@@ -1067,8 +1088,6 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   int rc = validate(cfg);
   if (rc) return rc;
   if (is_tangent(cfg->precision)) return PPL_E_INVAL;  // plain FP64 / FP32 states only
-  if (!f_in || !T_in || !f_out || !T_out || !stats_in || !stats_out || !status) return PPL_E_INVAL;
-  if (f_in == f_out || T_in == T_out) return PPL_E_INVAL;  // the step reads neighbours of what it writes
   for (int s = 0; s < 4; ++s)
     if (cfg->rho_w[s] || cfg->T_w[s] || cfg->T_dirichlet[s]) return PPL_E_INVAL;  // would need device copies
   double *scratch = nullptr;
@@ -1086,7 +1105,22 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   if (yblocks < 1) yblocks = 1;
   const int H = (cfg->ny + yblocks - 1) / yblocks;
   const dim3 grid(strips, (cfg->ny + H - 1) / H);
-  if ((long long)grid.x * grid.y > kNoAllocMaxCtas) return PPL_E_INVAL;  // beyond the static scratch
+  if ((long long)grid.x * grid.y > kNoAllocMaxCtas) return PPL_E_NOMEM;  // beyond the static scratch
+  // the caller's buffers (checked after the configuration, before anything is enqueued)
+  if (!f_in || !T_in || !f_out || !T_out || !stats_in || !stats_out || !status) return PPL_E_INVAL;
+  // 8-byte aligned state (the FP32 two-column kernel moves column pairs, FP64 moves doubles)
+  for (const void *p : {f_in, T_in, (const void *)f_out, (const void *)T_out})
+    if ((uintptr_t)p % 8 != 0) return PPL_E_INVAL;
+  {
+    // the step reads neighbours of what it writes: no output range may overlap another buffer
+    const size_t es = cfg->precision == PPL_FP64 ? sizeof(double) : sizeof(float);
+    const size_t nb = (size_t)cfg->nx * (size_t)cfg->ny * es;
+    const uintptr_t fi = (uintptr_t)f_in, ti = (uintptr_t)T_in, fo = (uintptr_t)f_out, to = (uintptr_t)T_out;
+    auto overlap = [](uintptr_t a, size_t na, uintptr_t b, size_t nb_) { return a < b + nb_ && b < a + na; };
+    if (overlap(fo, 9 * nb, fi, 9 * nb) || overlap(fo, 9 * nb, ti, nb) || overlap(to, nb, fi, 9 * nb) ||
+        overlap(to, nb, ti, nb) || overlap(fo, 9 * nb, to, nb))
+      return PPL_E_INVAL;
+  }
   // parameters of this configuration (a stack handle carries no device memory)
   ppl_sim tmp;
   tmp.cfg = *cfg;
