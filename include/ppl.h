@@ -183,6 +183,23 @@ int ppl_fields_device(ppl_t *h, void *rho, void *ux, void *uy, void *T, int dtyp
  * FP64 [9][ny][nx], decoded from the FP32 deviation storage when precision is FP32DEV. */
 int ppl_populations(ppl_t *h, double *f);
 
+/* The current state as FP64 device arrays: absolute populations f [9][ny][nx] (decoded
+ * from the FP32 deviation storage when precision is FP32DEV) and T [ny][nx], written into
+ * caller-owned device buffers (no allocation). The input of the adjoint sweep
+ * (ppl_adjoint_step). PPL_E_INVAL for sensitivity handles or NULL buffers. Synchronises. */
+int ppl_state_device(ppl_t *h, double *f, double *T);
+
+/* Device snapshot of the stored state (f, T and the step statistics in the working
+ * precision, exactly as the step kernel reads them), for checkpointed recomputation: the
+ * adjoint sweep restores a snapshot and steps forward again, bit-identically.
+ * ppl_snapshot_bytes: size of one snapshot (0 for NULL). ppl_snapshot copies into the
+ * caller's device buffer dst, ppl_restore copies src back and sets the step counter (which
+ * decides when the energy equation starts, iso_steps). Both are enqueued on the handle's
+ * stream and do not synchronise; dst / src stay caller-owned. */
+size_t ppl_snapshot_bytes(const ppl_t *h);
+int ppl_snapshot(ppl_t *h, void *dst);
+int ppl_restore(ppl_t *h, const void *src, int64_t step);
+
 /* Derivatives d rho, d u_x, d u_y, d T of the current state with respect to the parameter
  * of a sensitivity handle (PPL_FP64_D* or PPL_FP32_D*), as host FP64 [ny][nx] arrays (NULL
  * pointers skip a field). PPL_E_INVAL for other handles. Synchronises. */
@@ -249,6 +266,31 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
 
 /* Static description of a return code. */
 const char *ppl_strerror(int code);
+
+/*
+ * Reverse-mode (adjoint) sweep of one fused step, for the sigma / kappa calibration of
+ * Sec. 3.2 (Eqs. integral_coexistence_curve, surface_tension: sigma and kappa tuned per
+ * mesh) done on the lattice by gradient descent. For a scalar J of the state after the
+ * step, with fbar_in = dJ/df^{n+1}, it writes fbar_out = (df^{n+1}/df^n)^T fbar_in and adds
+ * (df^{n+1}/d sigma, df^{n+1}/d kappa)^T fbar_in to grad[0], grad[1] (FP64). The step is the
+ * one of Sec. 2 (Eqs. psi, peng-robinson, shanchen, Q, DensityAndVelocityRelationToF,
+ * collisionMRT, S, C, lbm) on the boxes the calibration uses: every side periodic,
+ * isothermal (energy_on = 0), no gravity, constant relaxation rates (eta_l, eta_v unset);
+ * other configurations return PPL_E_INVAL.
+ *
+ *  cfg        configuration of the forward step (sigma, kappa, rates, EOS)
+ *  f, T       device FP64 state of the step's input: absolute populations [9][ny][nx]
+ *             and T [ny][nx] (ppl_state_device gives them for any handle precision)
+ *  fbar_in    device FP64 [9][ny][nx]: dJ/df of the step's output
+ *  fbar_out   device FP64 [9][ny][nx]: dJ/df of the step's input; must not be fbar_in
+ *  grad       device FP64 [2], accumulated (+=) in a fixed order: bitwise reproducible
+ *  scratch    device workspace of ppl_adjoint_scratch_bytes(nx, ny) bytes, caller-owned
+ *  cuda_stream   stream to enqueue on (NULL: legacy default stream); nothing synchronises
+ * Returns PPL_OK, PPL_E_INVAL or PPL_E_CUDA.
+ */
+size_t ppl_adjoint_scratch_bytes(int32_t nx, int32_t ny);
+int ppl_adjoint_step(const ppl_config *cfg, const double *f, const double *T, const double *fbar_in,
+                     double *fbar_out, double *grad, void *scratch, void *cuda_stream);
 
 /* ---- host helpers of the refinement procedure (Sec. 3), FP64 ---- */
 
@@ -325,6 +367,23 @@ int ppl_batch_create(ppl_t *const *sims, const int32_t *substeps, int32_t n, ppl
  * Synchronises and returns the first non-OK status of the handles (PPL_E_NUMERIC). */
 int ppl_batch_step(ppl_batch_t *b, int64_t outer);
 void ppl_batch_destroy(ppl_batch_t *b);
+
+/* How a batch runs its outer steps (Sec. 3 refinement sequence, dt ~ dx^2).
+ * PPL_BATCH_GRAPH (the default): one CUDA graph per outer step whose concurrent branches
+ * launch each handle's steps. PPL_BATCH_PERSISTENT: one persistent launch per ppl_batch_step
+ * call, captured in a CUDA graph, for handles that all step with the FP32 two-column kernel
+ * (PPL_E_INVAL otherwise): resident CTAs take the tiles of every mesh's steps in time order
+ * from a ticket counter, each tile waiting until the previous step of its mesh is complete;
+ * results are bitwise those of stepping each handle by itself. Every such wait gives up
+ * after the batch's wait limit (default 1 s, ppl_batch_set_wait_limit, in ns); a wait that
+ * ran out stops the launch, sets PPL_FLAG_STALL in the handle's status word and makes
+ * ppl_batch_step return PPL_E_TIMEOUT, after which the handles' states are undefined
+ * (ppl_reset or ppl_load them). ppl_launch_count counts the steps a handle made. */
+#define PPL_BATCH_GRAPH 0
+#define PPL_BATCH_PERSISTENT 1
+int ppl_batch_set_mode(ppl_batch_t *b, int mode);
+int ppl_batch_get_mode(const ppl_batch_t *b);
+int ppl_batch_set_wait_limit(ppl_batch_t *b, int64_t ns);
 
 /* Liquid area of the current state for the droplet radius R(t) of Sec. 4.1:
  *   *area = sum over the nodes of clamp((rho - rho_lo) / (rho_hi - rho_lo), 0, 1)   (FP64),

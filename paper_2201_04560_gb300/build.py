@@ -16,8 +16,10 @@ UNITS = {
     "ppl.cu": [],
     "tools.cu": [],
     "thermo.cu": [],
+    "adjoint.cu": [],
     "step_fp64.cu": [],
     "step_fp32.cu": ["--use_fast_math"],
+    "batch_persist.cu": ["--use_fast_math"],
     "step_tangent.cu": [],
     "step_tangent32.cu": ["--use_fast_math"],
 }

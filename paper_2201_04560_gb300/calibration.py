@@ -180,3 +180,166 @@ def torch_observables(a, T_ratio, planar=None, laplace=None):
             return grad_out.to(torch.float64) @ jac
 
     return _Obs.apply
+
+
+# ---------------------------------------------------------------------------------------
+# Reverse mode: the adjoint of the fused step (ppl_adjoint_step) with checkpointed
+# recomputation, so that one reverse sweep gives the derivatives of a scalar with respect to
+# both parameters, whatever precision the forward run used.
+# ---------------------------------------------------------------------------------------
+class Tape:
+    """A forward run kept for a reverse sweep: the handle, and a device snapshot of its stored
+    state every `interval` steps. `fields` holds the final rho, u, T (host FP64).
+
+    reverse(dJ_drho) runs the sweep for a scalar J of the final state that depends on it
+    through rho (dJ_drho: [ny][nx]): segment by segment from the last, the segment's states
+    are recomputed from its snapshot and exported in FP64, and the adjoint steps run back
+    through them; d J / d(sigma, kappa) is accumulated in FP64 on the device."""
+
+    def __init__(self, cfg: dict, ic, steps: int, interval: int = 100):
+        import torch
+        self.cfg = dict(cfg)
+        self.steps, self.interval = int(steps), int(interval)
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self.sim = ppl.Simulation(cfg, *ic)
+        # the handle's steps, its snapshots and the adjoint steps share one stream, so that
+        # recomputing a segment never overwrites a tape the previous segment still reads
+        self.stream = torch.cuda.Stream()
+        self.sim.set_stream(self.stream)
+        self.snaps = []
+        done = 0
+        while done < self.steps:
+            buf = torch.empty(self.sim.snapshot_bytes, dtype=torch.uint8, device="cuda")
+            self.sim.snapshot(buf.data_ptr())
+            self.snaps.append((buf, done))
+            n = min(self.interval, self.steps - done)
+            self.sim.step(n)
+            done += n
+        self.fields = self.sim.fields()
+
+    def reverse(self, dJ_drho):
+        import numpy as np
+        import torch
+        nx, ny = self.nx, self.ny
+        seed = np.ascontiguousarray(np.broadcast_to(np.asarray(dJ_drho, dtype=np.float64), (9, ny, nx)))
+        lam = torch.from_numpy(seed).cuda()  # dJ/df_i = dJ/drho for every i (rho = sum f)
+        lam2 = torch.empty_like(lam)
+        grad = torch.zeros(2, dtype=torch.float64, device="cuda")
+        scratch = torch.empty(ppl.adjoint_scratch_bytes(nx, ny), dtype=torch.uint8, device="cuda")
+        tape_f = torch.empty((self.interval, 9, ny, nx), dtype=torch.float64, device="cuda")
+        tape_T = torch.empty((self.interval, ny, nx), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        for buf, step0 in reversed(self.snaps):
+            n = min(self.interval, self.steps - step0)
+            self.sim.restore(buf.data_ptr(), step0)
+            for m in range(n):
+                self.sim.state_device(tape_f[m].data_ptr(), tape_T[m].data_ptr())
+                if m + 1 < n:
+                    self.sim.step(1)
+            for m in reversed(range(n)):
+                ppl.adjoint_step(self.cfg, tape_f[m].data_ptr(), tape_T[m].data_ptr(), lam.data_ptr(),
+                                 lam2.data_ptr(), grad.data_ptr(), scratch.data_ptr(), self.stream)
+                lam, lam2 = lam2, lam
+        self.stream.synchronize()
+        return grad.cpu().numpy()
+
+    def close(self):
+        if self.sim is not None:
+            self.sim.close()
+            self.sim = None
+        self.snaps = []
+
+
+def planar_seed(rho):
+    """(rho_l, rho_v) of a planar slab (slab centre column nx/2, vapour column 0, averaged
+    across the strip) and their gradients with respect to the rho field."""
+    import numpy as np
+    ny, nx = rho.shape
+    gl, gv = np.zeros_like(rho), np.zeros_like(rho)
+    gl[:, nx // 2] = 1.0 / ny
+    gv[:, 0] = 1.0 / ny
+    return (float(rho[:, nx // 2].mean()), float(rho[:, 0].mean())), (gl, gv)
+
+
+def droplet_gamma_seed(rho, a, T, rv, rl):
+    """Laplace gamma = (p_in - p_out) R of a droplet field (the measure of _droplet_gamma) and
+    d gamma / d rho at every node."""
+    import numpy as np
+    lo, hi = 0.5 * (rl + rv) - 0.05 * (rl - rv), 0.5 * (rl + rv) + 0.05 * (rl - rv)
+    frac = (rho - lo) / (hi - lo)
+    A = float(np.clip(frac, 0.0, 1.0).sum())
+    R = math.sqrt(A / math.pi)
+    n = rho.shape[0]
+    c = n // 2
+    rin, rout = float(rho[c - 1:c + 1, c - 1:c + 1].mean()), float(rho[0, 0])
+    pin, dpin = ppl.pressure(a, EOS["b"], EOS["R"], EOS["omega"], T, rin)
+    pout, dpout = ppl.pressure(a, EOS["b"], EOS["R"], EOS["omega"], T, rout)
+    dP = pin - pout
+    g = np.where((frac > 0.0) & (frac < 1.0), dP / (2.0 * math.pi * R * (hi - lo)), 0.0)
+    g[c - 1:c + 1, c - 1:c + 1] += 0.25 * dpin * R
+    g[0, 0] -= dpout * R
+    return dP * R, g
+
+
+def _calibration_runs(a, T_ratio, sigma, kappa, precision, planar, laplace):
+    Tc, rv, rl = _coexistence(a, T_ratio)
+    T = T_ratio * Tc
+    nx, ny = planar.get("nx", 256), planar.get("ny", 8)
+    n = laplace.get("n", 128)
+    R0 = laplace.get("R0") or n / 4.0
+    cp = W.base_config(nx, ny, a=a, sigma=sigma, kappa=kappa, rho_l=rl, rho_v=rv, precision=precision,
+                       rho_ref=rv, T_ref=T)
+    icp = W.slab_fields(nx, ny, nx // 4, 3 * nx // 4, 3.0, rl, rv, T)
+    cd = W.base_config(n, n, a=a, sigma=sigma, kappa=kappa, rho_l=rl, rho_v=rv, precision=precision, rho_ref=rv,
+                       T_ref=T)
+    icd = W.droplet_fields(n, n, R0, 3.0, rl, rv, T, T)
+    return (cp, icp, planar.get("steps", 3000)), (cd, icd, laplace.get("steps", 3000)), (T, rv, rl)
+
+
+def adjoint_observables(a, T_ratio, sigma, kappa, weights, precision="fp32", interval=100, planar=None,
+                        laplace=None):
+    """(rho_l, rho_v, gamma) of the planar and droplet runs and d(w . obs)/d(sigma, kappa) for
+    the weights w, by two reverse sweeps (one per run) of the adjoint step."""
+    (cp, icp, sp), (cd, icd, sd), (T, rv, rl) = _calibration_runs(a, T_ratio, sigma, kappa, precision,
+                                                                  dict(planar or {}), dict(laplace or {}))
+    tp = Tape(cp, icp, sp, interval)
+    (rho_l, rho_v), (gl, gv) = planar_seed(tp.fields["rho"])
+    grad = tp.reverse(weights[0] * gl + weights[1] * gv)
+    tp.close()
+    td = Tape(cd, icd, sd, interval)
+    gamma, gg = droplet_gamma_seed(td.fields["rho"], a, T, rv, rl)
+    grad = grad + td.reverse(weights[2] * gg)
+    td.close()
+    return [rho_l, rho_v, gamma], grad
+
+
+def torch_observables_adjoint(a, T_ratio, precision="fp32", interval=100, planar=None, laplace=None):
+    """torch.autograd.Function mapping (sigma, kappa) to (rho_l, rho_v, gamma) whose backward
+    is the adjoint of the fused step: the forward runs (FP32 by default) keep checkpoints every
+    `interval` steps, and backward() runs one reverse sweep per run for the incoming
+    vector-Jacobian weights, with FP64 accumulation of the parameter gradient."""
+    import torch
+
+    class _Obs(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params):
+            (cp, icp, sp), (cd, icd, sd), (T, rv, rl) = _calibration_runs(
+                a, T_ratio, float(params[0]), float(params[1]), precision, dict(planar or {}), dict(laplace or {}))
+            tp, td = Tape(cp, icp, sp, interval), Tape(cd, icd, sd, interval)
+            (rho_l, rho_v), (gl, gv) = planar_seed(tp.fields["rho"])
+            gamma, gg = droplet_gamma_seed(td.fields["rho"], a, T, rv, rl)
+            ctx.tapes = (tp, td)
+            ctx.seeds = (gl, gv, gg)
+            return torch.tensor([rho_l, rho_v, gamma], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            tp, td = ctx.tapes
+            gl, gv, gg = ctx.seeds
+            w = [float(v) for v in grad_out]
+            grad = tp.reverse(w[0] * gl + w[1] * gv) + td.reverse(w[2] * gg)
+            tp.close()
+            td.close()
+            return torch.tensor(grad, dtype=torch.float64)
+
+    return _Obs.apply

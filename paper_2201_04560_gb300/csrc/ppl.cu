@@ -960,6 +960,45 @@ int ppl_populations(ppl_t *h, double *f) {
   return rc;
 }
 
+int ppl_state_device(ppl_t *h, double *f, double *T) {
+  if (!h || !f || !T || is_tangent(h->prec)) return PPL_E_INVAL;
+  const int nt = 256;
+  const unsigned blocks = (unsigned)((h->N + nt - 1) / nt);
+  if (h->prec == PPL_FP64)
+    export_populations<double><<<blocks, nt, 0, h->stream>>>(h->pd, (const double *)h->f[h->cur], f);
+  else
+    export_populations<float><<<blocks, nt, 0, h->stream>>>(h->pf, (const float *)h->f[h->cur], f);
+  CK(cudaGetLastError());
+  return export_device(h, nullptr, nullptr, nullptr, T, 0);
+}
+
+size_t ppl_snapshot_bytes(const ppl_t *h) {
+  return h ? (size_t)10 * h->N * h->rsz + 4 * sizeof(double) : 0;
+}
+
+int ppl_snapshot(ppl_t *h, void *dst) {
+  if (!h || !dst) return PPL_E_INVAL;
+  unsigned char *d = (unsigned char *)dst;
+  const size_t fb = (size_t)9 * h->N * h->rsz, tb = (size_t)h->N * h->rsz;
+  CK(cudaMemcpyAsync(d, h->f[h->cur], fb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + fb, h->T[h->cur], tb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(d + fb + tb, h->stats[h->cur], 4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return PPL_OK;
+}
+
+int ppl_restore(ppl_t *h, const void *src, int64_t step) {
+  if (!h || !src || step < 0) return PPL_E_INVAL;
+  const unsigned char *d = (const unsigned char *)src;
+  const size_t fb = (size_t)9 * h->N * h->rsz, tb = (size_t)h->N * h->rsz;
+  h->cur = 0;
+  CK(cudaMemcpyAsync(h->f[0], d, fb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->T[0], d + fb, tb, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->stats[0], d + fb + tb, 4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+  h->step = step;
+  return PPL_OK;
+}
+
 int ppl_norms(ppl_t *h, ppl_norms_t *out) {
   if (!h || !out) return PPL_E_INVAL;
   int rc = stats(h, nullptr);

@@ -114,9 +114,13 @@ constexpr size_t row_step_smem_bytes() {
 // every thread) is written to its slot; the last CTA to finish sums the slots in a fixed
 // order and publishes rho_bar and the mass for the next step. TANGENT: dacc carries the
 // derivative of the sum as well (two slots per CTA), published as d rho_bar.
+// The tile of a step is CTA `bid` of `nblk` (blockIdx / gridDim for a step launch); `done`, if
+// given, is set to `done_value` (release) by the last tile once rho_bar is published (the
+// persistent batch's step-completion flag).
 template <int NT, bool TANGENT, typename PT>
-__device__ __forceinline__ void block_mass_finalize(const Params<PT> &P, const StepIO &io, double acc,
-                                                    double dacc) {
+__device__ __forceinline__ void tile_mass_finalize(const Params<PT> &P, const StepIO &io, double acc, double dacc,
+                                                   unsigned bid, unsigned nblk, unsigned *done = nullptr,
+                                                   unsigned done_value = 0) {
   const int t = threadIdx.x;
   constexpr int K = TANGENT ? 2 : 1;
   __shared__ double red[K][NT / 32];
@@ -131,8 +135,6 @@ __device__ __forceinline__ void block_mass_finalize(const Params<PT> &P, const S
     if ((t & 31) == 0) red[j][t >> 5] = v[j];
   }
   __syncthreads();
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
   if (t == 0) {
     for (int j = 0; j < K; ++j) {
       double s = 0.0;
@@ -169,8 +171,19 @@ __device__ __forceinline__ void block_mass_finalize(const Params<PT> &P, const S
       io.stats_out[1] = tot[0];
       if (TANGENT) io.stats_out[2] = tot[K - 1] * P.inv_nodes;
       *io.counter = 0u;
+      if (done) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(done), "r"(done_value) : "memory");
+      }
     }
   }
+  __syncthreads();  // the shared reduction slots may be reused by the caller's next tile
+}
+
+template <int NT, bool TANGENT, typename PT>
+__device__ __forceinline__ void block_mass_finalize(const Params<PT> &P, const StepIO &io, double acc,
+                                                    double dacc) {
+  tile_mass_finalize<NT, TANGENT>(P, io, acc, dacc, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
 }
 
 // SIMPLE: every row the CTA touches is an interior row (no wall, outflow or periodic

@@ -2,24 +2,41 @@
 // are hydrodynamically periodic in x, with an even nx (the x lines may hold Dirichlet
 // temperatures).
 //
-// The same row-marching pipeline as row_step.cuh (stages S1..S4 at row lags 0..3, rings
-// of per-row quantities in shared memory), with each thread owning the adjacent columns
+// The row-marching pipeline of row_step.cuh with each thread owning the adjacent columns
 // (2t, 2t + 1) of a strip of 2 NT columns: 4 halo columns on each side, 2 NT - 8 interior
 // columns. Both columns of a thread are computed by one packed instruction wherever the
 // arithmetic allows (F2 in lane2.cuh), the staged rows and the stores move 8 bytes per
 // thread, and a column's neighbours come from one 8-byte and two 4-byte shared-memory
 // reads per pair (ring rows carry two zeroed pad floats on each side, so the reads of the
 // strip's outermost threads need no clamping: those columns are halo, never stored). With
-// x periodic and nx even, a pair never straddles the domain edge
-// and its global address is 8-byte aligned. Rows (walls, outflow, Dirichlet lines in y)
-// are handled exactly as in the one-column kernel; only per-node boundary data of a wall
-// row (rho_w, T_w, the Dirichlet mask) is looked up column by column.
+// x periodic and nx even, a pair never straddles the domain edge and its global address is
+// 8-byte aligned. Rows (walls, outflow, Dirichlet lines in y) are handled as in the
+// one-column kernel; only per-node boundary data of a wall row (rho_w, T_w, the Dirichlet
+// mask) is looked up column by column.
+//
+// Stages and row lags of one iteration (row q staged):
+//   S1 (row q):   rho, j = sum f c, psi                                   Eqs. (psi), (peng-robinson)
+//   S2 (row q-1): F^m (+ psi-based wall form), F^b, Q, u, and the MRT     Eqs. (shanchen), (shanchen-walls),
+//                 collision with the Li source terms                      (psi-based-formula), (Q), (Q-psi-based),
+//                                                                         (gravitational_force), (collisionMRT),
+//                                                                         (li_source_terms), (S), (C)
+//   S3 (row q-2): pull streaming, Zou-He, store of f and the mass        Eq. (lbm), Sec. 2.2;
+//                 partial; first Heun stage of the energy equation        Eq. (energy-equation)
+//   S4 (row q-3): second Heun stage, store of T
+// Every per-row quantity lives in a ring of three rows (row mod 3): psi and rho (rows q .. q-2),
+// T (rows q .. q-2), u (rows q-1 .. q-3), the sideways post-collision populations (rows q-1 ..
+// q-3), the first Heun stage T* (rows q-2 .. q-4) and the staged rows (q-1 .. q+1). The
+// stencils of the first Heun stage reach rho and T one row further down (q-3); that row's
+// share of each stencil is formed one iteration earlier, when the row is the stencil's
+// centre, and kept in thread-private shared memory. With every ring of period three, the
+// slots are addressed through three per-thread pointers that rotate once per iteration,
+// so every ring access is a fixed offset from one of them.
 //
 // Row staging: a strip that lies wholly inside the domain has each row brought in by TMA
 // (one thread issues a 3-D tensor copy of the nine population rows and a 2-D copy of the
-// temperature row, completing on the slot's mbarrier, which all threads wait on); strips
-// that wrap across the periodic x seam, and domains without tensor maps, use per-thread
-// 8-byte cp.async copies with the wrap applied per column.
+// temperature row, completing on the slot's mbarrier, which all threads wait on) two rows
+// ahead; strips that wrap across the periodic x seam, and domains without tensor maps, use
+// per-thread 8-byte cp.async copies one row ahead, with the wrap applied per column.
 #pragma once
 
 #include "lane2.cuh"
@@ -36,6 +53,11 @@ __device__ __forceinline__ Trip trip(const float *row, int t) {
   const float l = row[2 * t - 1], r = row[2 * t + 2];
   return {F2(l, c.x), F2(c), F2(c.y, r)};
 }
+// the same three pairs, from a pointer already at the thread's column 2t
+__device__ __forceinline__ Trip tripp(const float *p) {
+  const float2 c = *reinterpret_cast<const float2 *>(p);
+  return {F2(p[-1], c.x), F2(c), F2(c.y, p[2])};
+}
 __device__ __forceinline__ F2 ld2(const float *p) { return F2(*reinterpret_cast<const float2 *>(p)); }
 __device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<float2 *>(p) = v.v; }
 __device__ __forceinline__ void cp_async8(float *smem_dst, const float *gmem_src) {
@@ -43,9 +65,6 @@ __device__ __forceinline__ void cp_async8(float *smem_dst, const float *gmem_src
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
-// staged rows [PF + 3][10][2 NT]; rings of row stride 2 NT + 4: psi, rho, T, ux, uy [4] (row
-// mod 4) and [3][7] (row mod 3: the six sideways post-collision populations and the first
-// Heun stage T*)
 // ---- TMA row staging: bulk tensor copies completing on an mbarrier (sm_90+) ----
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
@@ -96,37 +115,53 @@ template <int NT>
 __host__ __device__ constexpr int pair_ring_stride() {
   return 2 * NT + 4;
 }
-template <int NT, int PF>
+constexpr int kPairSlots = 3;      // staged rows and ring rows per quantity
+constexpr int kPairRingRows = 12;  // ring rows per slot: psi, rho, T, ux, uy, f*_{1,3,5,6,7,8}, T*
+constexpr int kPairShareRows = 5;  // a row's shares of the stencils of the row above (thread-private)
+template <int NT>
 constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is aligned up to 128 bytes
-  return (size_t)((PF + 3) * 10 * (2 * NT) + (5 * 4 + 3 * 7) * pair_ring_stride<NT>()) * sizeof(float) + 128;
+  return (size_t)(kPairSlots * 10 * (2 * NT) + (kPairSlots * kPairRingRows + kPairShareRows) * pair_ring_stride<NT>()) *
+             sizeof(float) +
+         128;
 }
 
-template <bool ENERGY, int NT, int PF, bool SIMPLE>
-__device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int H,
-                                              unsigned char *smem_raw, unsigned long long *bars) {
-  constexpr int D = PF + 3;
+// first Heun stage of a row, handed from S3 to S4 of the next iteration
+struct PairHeun {
+  F2 k1, lam, gdx, gdy, div, inv_rcv, A, B, T0;
+};
+
+// One tile of the step: strip bx (2 NT - 8 interior columns) and row block by (H rows), CTA
+// bid of nblk for the mass reduction; `done` as in tile_mass_finalize.
+template <bool ENERGY, int NT, bool SIMPLE>
+__device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int H, int bx, int by,
+                                              unsigned bid, unsigned nblk, unsigned char *smem_raw,
+                                              unsigned long long *bars, unsigned *done = nullptr,
+                                              unsigned done_value = 0) {
   constexpr int SW = 2 * NT;  // strip columns
   constexpr int W = SW - 8;   // interior columns
   static_assert(W % 4 == 0, "strip starts must stay 16-byte aligned for the TMA copies");
   constexpr int RS = pair_ring_stride<NT>();
-  constexpr int NRING = 5 * 4 + 3 * 7;  // ring rows
+  constexpr int NRING = kPairSlots * kPairRingRows;
   const unsigned raw_s = (unsigned)__cvta_generic_to_shared(smem_raw);
-  float *stg = reinterpret_cast<float *>(smem_raw + ((128u - (raw_s & 127u)) & 127u));  // [D][10][SW]
-  float *rings = stg + D * 10 * SW;
-  // ring pointers address column 0 of slot 0; columns -2, -1, SW, SW + 1 are the pads
-  float *rpsi = rings + 2;  // [4][RS], row mod 4
-  float *rrho = rpsi + 4 * RS;
-  float *rT = rrho + 4 * RS;
-  float *rux = rT + 4 * RS;
-  float *ruy = rux + 4 * RS;
-  float *rfs = ruy + 4 * RS;  // [3][7][RS], row mod 3: f*_1, f*_3, f*_5, f*_6, f*_7, f*_8, T*
+  float *stg = reinterpret_cast<float *>(smem_raw + ((128u - (raw_s & 127u)) & 127u));  // [3][10][SW]
+  float *rings = stg + kPairSlots * 10 * SW;
+  // ring row (quantity k, slot s) at rings + (s * kPairRingRows + k) * RS + 2; columns -2, -1,
+  // SW, SW + 1 are the pads
+  // ring rows of a slot s at rings + (s * kPairRingRows + k) * RS + 2 for quantity k (columns
+  // -2, -1, SW, SW + 1 are the pads); the slots are addressed by role through three rotating
+  // per-thread pointers (below), so every ring access is a fixed offset from one of them
+  // shares of the stencils of the first Heun stage that the row below the centre contributes
+  // (grad rho x, y; grad T x, y; Laplacian of T), formed when that row was the centre; each
+  // thread reads back only its own columns
+  float *share = rings + kPairSlots * kPairRingRows * RS + 2 + 2 * threadIdx.x;
+  enum { R_PSI = 0, R_RHO = 1, R_T = 2, R_UX = 3, R_UY = 4, R_F1 = 5, R_TS = 11 };
   const float third = 1.0f / 3.0f, twelfth = 1.0f / 12.0f;
   const float big = 3.0e38f;
 
   const int t = threadIdx.x;
   const int c2 = 2 * t;  // strip column of lane 0
-  const int x0 = blockIdx.x * W;
-  const int ya = blockIdx.y * H;
+  const int x0 = bx * W;
+  const int ya = by * H;
   const int yb = min(ya + H, P.ny);
   const int gx0 = x0 - 4 + c2;  // even
   int src0 = gx0 % P.nx;
@@ -137,11 +172,11 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   const long long plane = P.plane;
   const float rho_bar = (float)io.stats_in[0];
   const bool any_outflow = P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
-  const bool t_s4 = t >= 2 && t < NT - 2 && gx0 < P.nx;  // both lanes interior and in the domain
+  const bool t_in = t >= 2 && t < NT - 2 && gx0 < P.nx;  // both lanes interior and in the domain
   const float *fin = reinterpret_cast<const float *>(io.f_in) + src0;
   const float *Tin = reinterpret_cast<const float *>(io.T_in) + src0;
-  float *fout = reinterpret_cast<float *>(io.f_out);
-  float *Tout = reinterpret_cast<float *>(io.T_out);
+  float *fout = reinterpret_cast<float *>(io.f_out) + gx0;
+  float *Tout = reinterpret_cast<float *>(io.T_out) + gx0;
   const int n_it = yb - ya + 6;
   unsigned flags = 0;
   F2 acc_s(0.0f), acc_n(0.0f);  // compensated per-lane mass sums (acc_n: minus the compensation)
@@ -166,60 +201,61 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   const unsigned stg_s = (unsigned)__cvta_generic_to_shared(stg);
   const unsigned bar_s = (unsigned)__cvta_generic_to_shared(bars);
   if (use_tma && t == 0) {
-    for (int j = 0; j < D; ++j) mbar_init(bar_s + 8 * j, 1);
+    for (int j = 0; j < kPairSlots; ++j) mbar_init(bar_s + 8 * j, 1);
     mbar_fence_init();
     tmap_acquire(io.tmap_f);
     tmap_acquire(io.tmap_T);
   }
+  for (int i = t; i < NRING * 4; i += NT) rings[(i >> 2) * RS + ((i & 3) < 2 ? (i & 3) : SW + (i & 3))] = 0.0f;
   __syncthreads();
-  auto stage_row = [&](int q, int slot) {
+  // row q into staging slot `slot` (TMA, one thread), or into this thread's columns at dst
+  auto stage_row = [&](int q, int slot, const float *dst_c) {
     const int src = row_map(q).src;
     if (use_tma) {
       if (t == 0) tma_row<NT>(stg_s + slot * 10 * SW * 4, bar_s + 8 * slot, io.tmap_f, io.tmap_T, x0 - 4, src);
       return;
     }
     const long long k = (long long)src * P.nx;
-    float *dst = stg + slot * 10 * SW + c2;
+    float *dst = const_cast<float *>(dst_c);
 #pragma unroll
     for (int i = 0; i < 9; ++i) cp_async8(dst + i * SW, fin + i * plane + k);
     cp_async8(dst + 9 * SW, Tin + k);
   };
-  for (int i = t; i < NRING * 4; i += NT) rings[(i >> 2) * RS + ((i & 3) < 2 ? (i & 3) : SW + (i & 3))] = 0.0f;
+  // rows ya - 3 and ya - 2 go out before the loop: by TMA both (two rows ahead), by cp.async
+  // the first (one row ahead; each iteration stages the next)
+  stage_row(ya - 3, 0, stg + c2);
+  cp_async_commit();
+  if (use_tma && n_it > 1) stage_row(ya - 2, 1, nullptr);
 
-#pragma unroll
-  for (int j = 0; j < PF; ++j) {
-    if (j < n_it) stage_row(ya - 3 + j, j);
-    cp_async_commit();
-  }
-  // TMA runs TL = D - 2 rows ahead: row q + TL goes into the slot of row q - 2 as soon as the
-  // collision stage has read it, one stage earlier than a copy issued at the next iteration
-  constexpr int TL = D - 2;
-  if (use_tma)
-    for (int j = PF; j < TL; ++j)
-      if (j < n_it) stage_row(ya - 3 + j, j);
+  // Slot roles: 0 holds rows q and q - 3, 1 rows q - 1 and q - 4, 2 rows q - 2 and q + 1.
+  // Each iteration rotates the roles (0, 1, 2) <- (2, 0, 1).
+  float *r0 = rings + 0 * kPairRingRows * RS + 2 + c2, *r1 = rings + 2 * kPairRingRows * RS + 2 + c2,
+        *r2 = rings + 1 * kPairRingRows * RS + 2 + c2;
+  const float *g0 = stg + 0 * 10 * SW + c2, *g1 = stg + 2 * 10 * SW + c2, *g2 = stg + 1 * 10 * SW + c2;
+  int k0 = 0, k1 = 2, k2 = 1;  // slot numbers of the roles (TMA destination, mbarrier)
+  unsigned ph = 0;              // mbarrier parity per slot (bit k)
+  // values carried between stages and iterations, by row
+  F2 jn_x(0.0f), jn_y(0.0f), jc_x(0.0f), jc_y(0.0f);  // S1 (row q) -> S2 (row q - 1, next iteration)
+  F2 f0n(0.0f), f0c(0.0f);                             // S2 (row q - 1) -> S3 (row q - 2, next)
+  F2 f2n(0.0f), f2c(0.0f), f2cc(0.0f);                 // f_2 of rows q - 1, q - 2, q - 3
+  F2 Fxn(0.0f), Fyn(0.0f), Fxc(0.0f), Fyc(0.0f), irn(0.0f), irc(0.0f);  // F and 1/rho, S2 -> S3
+  F2 f4(0.0f);  // post-collision f_4 of row q - 1, streamed down into row q - 2 in the same iteration
+  PairHeun nxt{}, cur{};  // S3 (row q - 2) -> S4 (row q - 3, next iteration)
 
-  F2 c1jx(0.0f), c1jy(0.0f), n1jx(0.0f), n1jy(0.0f);
-  F2 f0n(0.0f), f2n(0.0f), f4n(0.0f), f0c(0.0f), f2c1(0.0f), f2c2(0.0f);
-  S3Carry<F2> cc2{}, nn2{};
-  S4Carry<F2> cur{}, nxt{};
-  int f3 = 0;
   for (int iq = 0; iq < n_it; ++iq) {
     const int q = ya - 3 + iq;
-    if (!use_tma && iq + PF < n_it) stage_row(q + PF, (iq + PF) % D);
-    bool stalled = false;
-    if (use_tma) {
-      stalled = !mbar_wait(bar_s + 8 * (iq % D), (iq / D) & 1);  // row q has landed
-    } else {
+    if (!use_tma) {
+      if (iq + 1 < n_it) stage_row(q + 1, k2, g2);
       cp_async_commit();
-      cp_async_wait<PF>();  // this thread's copies of row q have landed
+      cp_async_wait<1>();  // this thread's copies of row q have landed
     }
-    const int s4_0 = iq & 3, s4_1 = (iq + 3) & 3, s4_2 = (iq + 2) & 3, s4_3 = (iq + 1) & 3;
-    const int f_r3 = f3, f_r2 = f3 == 2 ? 0 : f3 + 1, f_r4 = f3 == 0 ? 2 : f3 - 1;
+    bool stalled = false;
+    if (use_tma) stalled = !mbar_wait(bar_s + 8 * k0, (ph >> k0) & 1u);  // row q has landed
 
     // ---- S1: row q ----
     {
       const LineMap rm = row_map(q);
-      const float *st = stg + (iq % D) * 10 * SW + c2;
+      const float *st = g0;
       F2 f[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i] = ld2(st + i * SW);
@@ -232,34 +268,34 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         arg_min = fminf(arg_min, fminf(arg.lo(), arg.hi()));
         psi = sqrt(fmax(arg, F2(0.0f)));
       }
-      const int i0 = s4_0 * RS + c2;
-      st2(rpsi + i0, psi);
-      st2(rrho + i0, rho);
-      st2(rT + i0, Tt);
+      st2(r0 + (R_PSI) * RS, psi);
+      st2(r0 + (R_RHO) * RS, rho);
+      st2(r0 + (R_T) * RS, Tt);
       const F2 d57 = f[5] - f[7], d68 = f[6] - f[8];
-      n1jx = (f[1] - f[3]) + (d57 - d68);
-      n1jy = (f[2] - f[4]) + (d57 + d68);
+      jn_x = (f[1] - f[3]) + (d57 - d68);
+      jn_y = (f[2] - f[4]) + (d57 + d68);
     }
     if (use_tma) {
       // a row that did not land stops the CTA (uniformly): the copies already issued are
       // waited for (bounded) before it leaves, and the status word reports the step invalid
       if (__syncthreads_or(stalled)) {
         flags |= FLAG_STALL;
-        if (t == 0)
-          for (int n = iq; n <= min(iq + TL - 1, n_it - 1); ++n) mbar_wait(bar_s + 8 * (n % D), (n / D) & 1);
+        if (t == 0) {
+          mbar_wait(bar_s + 8 * k0, (ph >> k0) & 1u);
+          if (iq + 1 < n_it) mbar_wait(bar_s + 8 * k2, (ph >> k2) & 1u);
+        }
         break;
       }
     } else {
       __syncthreads();
     }
 
-    // ---- S2: row q-1 ----
+    // ---- S2: row q-1 (forces, velocity, collision) ----
     if (iq >= 2) {
       const int r = q - 1;
       const LineMap rm = row_map(r);
-      const int i0 = s4_1 * RS, iu = s4_0 * RS, id = s4_2 * RS;
       if (!rm.solid) {
-        const Trip pu = trip(rpsi + iu, t), pm = trip(rpsi + i0, t), pd = trip(rpsi + id, t);
+        const Trip pu = tripp(r0 + (R_PSI) * RS), pm = tripp(r1 + (R_PSI) * RS), pd = tripp(r2 + (R_PSI) * RS);
         const F2 p1 = pm.r, p3 = pm.l, p2 = pu.c, p4 = pd.c, p5 = pu.r, p6 = pu.l, p7 = pd.l, p8 = pd.r;
         const F2 psi_c = pm.c;
         const F2 d57 = p5 - p7, d86 = p8 - p6, s57 = p5 + p7, s68 = p6 + p8, s13 = p1 + p3, s24 = p2 + p4;
@@ -278,7 +314,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
             pf = P.Gw_over_G * psi_c;
             pq = psi_c;
           } else {
-            const F2 Tw = P.T_ref + ld2(rT + i0 + c2);
+            const F2 Tw = P.T_ref + ld2(r1 + (R_T) * RS);
             const float a0 = psi_arg(P, wall_rho_w(P, ws, col0, rm.src), Tw.lo());
             const float a1 = psi_arg(P, wall_rho_w(P, ws, col1, rm.src), Tw.hi());
             if (!(a0 >= 0.0f) || !(a1 >= 0.0f)) flags |= FLAG_PSI_NEG;
@@ -291,173 +327,197 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           qd = qd - third * pq;
         }
         const F2 qf = P.kappa_G2 * psi_c;
-        nn2.qs = qf * qs;
-        nn2.qd = qf * qd;
-        nn2.qxy = qf * qxy;
-        const F2 rho = ld2(rrho + i0 + c2);
+        const F2 rho = ld2(r1 + (R_RHO) * RS);
         const F2 gps = (-P.G) * psi_c;
         const F2 fmx = gps * sx, fmy = gps * sy;
         const F2 Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
         const F2 inv_rho = 1.0f / rho;
-        const F2 ux = (c1jx + 0.5f * Fx) * inv_rho;
-        const F2 uy = (c1jy + 0.5f * Fy) * inv_rho;
-        st2(rux + i0 + c2, ux);
-        st2(ruy + i0 + c2, uy);
-        nn2.fmx = fmx;
-        nn2.fmy = fmy;
-        nn2.fm2 = (P.G * P.G) * (sx * sx + sy * sy);
-        nn2.inv_rho = inv_rho;
-        if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1
-          st2(rux + s4_3 * RS + c2, ux);
-          st2(ruy + s4_3 * RS + c2, -uy);
+        const F2 ux = (jc_x + 0.5f * Fx) * inv_rho;
+        const F2 uy = (jc_y + 0.5f * Fy) * inv_rho;
+        st2(r1 + (R_UX) * RS, ux);
+        st2(r1 + (R_UY) * RS, uy);
+        if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1 (slot of row q - 3)
+          st2(r0 + (R_UX) * RS, ux);
+          st2(r0 + (R_UY) * RS, -uy);
         }
-      } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny
-        st2(rux + i0 + c2, ld2(rux + s4_3 * RS + c2));
-        st2(ruy + i0 + c2, -ld2(ruy + s4_3 * RS + c2));
-      }
-      __syncthreads();
-    }
-
-    // ---- S3: row q-2 ----
-    if (iq >= 4) {
-      const int r = q - 2;
-      const LineMap rm = row_map(r);
-      const int i0 = s4_2 * RS, iu = s4_1 * RS, id = s4_3 * RS;
-      float *fs = rfs + f_r2 * 7 * RS + c2;  // this row's f* and T* slot
-      if (!rm.solid) {
-        const float *st = stg + ((iq + D - 2) % D) * 10 * SW + c2;
+        // collision of the staged row q - 1
+        const float *st = g1;
         F2 fd[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fd[i] = ld2(st + i * SW);
-        const F2 rho = ld2(rrho + i0 + c2);
-        const F2 ux = ld2(rux + i0 + c2), uy = ld2(ruy + i0 + c2);
-        const F2 Fx = cc2.fmx + P.gx * (rho - rho_bar), Fy = cc2.fmy + P.gy * (rho - rho_bar);
         F2 e(P.e_const);  // s_eta / 4
         if (P.var_eta) e = 1.0f / (P.e_c0 + P.e_c1 * rho);
-        collide(P, fd, rho, ux, uy, Fx, Fy, cc2.fm2, cc2.qs, cc2.qd, cc2.qxy, e);
-        st2(fs + 0 * RS, fd[1]);
-        st2(fs + 1 * RS, fd[3]);
-        st2(fs + 2 * RS, fd[5]);
-        st2(fs + 3 * RS, fd[6]);
-        st2(fs + 4 * RS, fd[7]);
-        st2(fs + 5 * RS, fd[8]);
+        const F2 fm2 = (P.G * P.G) * (sx * sx + sy * sy);
+        collide(P, fd, rho, ux, uy, Fx, Fy, fm2, ev(qf * qs), ev(qf * qd), ev(qf * qxy), e);
+        st2(r1 + (R_F1 + 0) * RS, fd[1]);
+        st2(r1 + (R_F1 + 1) * RS, fd[3]);
+        st2(r1 + (R_F1 + 2) * RS, fd[5]);
+        st2(r1 + (R_F1 + 3) * RS, fd[6]);
+        st2(r1 + (R_F1 + 4) * RS, fd[7]);
+        st2(r1 + (R_F1 + 5) * RS, fd[8]);
         f0n = fd[0];
         f2n = fd[2];
-        f4n = fd[4];
-        nxt.Fx = Fx;
-        nxt.Fy = Fy;
-        if (ENERGY) {
-          const F2 T0 = ld2(rT + i0 + c2);
-          nxt.ux = ux;
-          nxt.uy = uy;
-          pr_parts(P, rho, &nxt.A, &nxt.B);
-          nxt.inv_rcv = cc2.inv_rho * P.cv_inv;
-          nxt.lam = P.lam_v + P.dlam * (rho - P.rho_v);
-          const Trip ru = trip(rrho + iu, t), rmd = trip(rrho + i0, t), rd = trip(rrho + id, t);
-          nxt.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l - rd.l + rd.r));
-          nxt.gdy = P.dlam * (third * (ru.c - rd.c) + twelfth * (ru.r + ru.l - rd.l - rd.r));
-          const Trip xu = trip(rux + iu, t), xm = trip(rux + i0, t), xd = trip(rux + id, t);
-          const Trip yu = trip(ruy + iu, t), yd = trip(ruy + id, t);
-          nxt.div = third * (xm.r - xm.l) + twelfth * (xu.r - xu.l - xd.l + xd.r) + third * (yu.c - yd.c) +
-                    twelfth * (yu.r + yu.l - yd.l - yd.r);
-          F2 Ts;
-          if (!SIMPLE && rm.outflow) {
-            Ts = ld2(rfs + f_r3 * 7 * RS + 6 * RS + c2);  // outflow row: copy of the first interior row
-            nxt.k1 = F2(0.0f);
-          } else {
-            const Trip tu = trip(rT + iu, t), tm = trip(rT + i0, t), td = trip(rT + id, t);
-            const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
-            const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
-            const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * T0) +
-                           (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * T0);
-            // (lambda lap T + grad lambda . grad T - T (dp/dT) div u) / (rho c_v) - u . grad T
-            const F2 adv = ux * gtx + uy * gty;
-            const F2 cond = nxt.lam * lap + nxt.gdx * gtx + nxt.gdy * gty;
-            const F2 comp = T_dpdT(P, nxt.A, nxt.B, P.T_ref + T0) * nxt.div;
-            const F2 k1 = ev((cond - comp) * nxt.inv_rcv) - adv;
-            nxt.k1 = k1;
-            Ts = T0 + k1;
-            if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes of a boundary line
-              float tw0, tw1;
-              const bool d0 = t_fixed(P, col0, rm.src, &tw0), d1 = t_fixed(P, col1, rm.src, &tw1);
-              if (d0 || d1) {
-                Ts = F2(d0 ? tw0 - P.T_ref : Ts.lo(), d1 ? tw1 - P.T_ref : Ts.hi());
-                nxt.k1 = F2(d0 ? 0.0f : k1.lo(), d1 ? 0.0f : k1.hi());
-              }
-            }
-          }
-          st2(fs + 6 * RS, Ts);
-          if (!SIMPLE && r == 1 && P.hbc[2] == WALL) st2(rfs + f_r4 * 7 * RS + 6 * RS + c2, Ts);  // mirror ghost of row -1
-        }
-      } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {
-        st2(fs + 6 * RS, ld2(rfs + f_r4 * 7 * RS + 6 * RS + c2));  // mirror ghost of row ny
+        f4 = fd[4];
+        Fxn = Fx;
+        Fyn = Fy;
+        irn = inv_rho;
+      } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny = row ny - 2
+        st2(r1 + (R_UX) * RS, ld2(r0 + (R_UX) * RS));
+        st2(r1 + (R_UY) * RS, -ld2(r0 + (R_UY) * RS));
       }
       __syncthreads();
     }
-    // the slot of row q - 2 is free (its last reader, the collision stage, is past a barrier;
-    // before iteration 4 its row was read by the first stage only)
-    if (use_tma && iq + TL < n_it) stage_row(q + TL, (iq + TL) % D);
+    // the slot of row q - 1 is free (its last reader, the collision, is past a barrier; before
+    // iteration 2 its row was read by the first stage only): row q + 2 goes into it
+    if (use_tma && iq + 2 < n_it) stage_row(q + 2, k1, nullptr);
 
-    // ---- S4: row q-3 ----
-    if (iq >= 6 && t_s4) {
-      const int r = q - 3;
+    // ---- S3: row q-2 (streaming, store of f; first Heun stage) ----
+    if (iq >= 3) {
+      const int r = q - 2;
       const LineMap rm = row_map(r);
-      if (!rm.outflow) {
+      if (iq >= 5 && r < yb && t_in && !rm.outflow) {
         // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi)
-        const float *lo = rfs + f_r4 * 7 * RS, *mid = rfs + f_r3 * 7 * RS, *hi = rfs + f_r2 * 7 * RS;
         F2 fd[9];
         fd[0] = f0c;
-        fd[1] = trip(mid + 0 * RS, t).l;
-        fd[2] = f2c2;
-        fd[3] = trip(mid + 1 * RS, t).r;
-        fd[4] = f4n;
-        fd[5] = trip(lo + 2 * RS, t).l;
-        fd[6] = trip(lo + 3 * RS, t).r;
-        fd[7] = trip(hi + 4 * RS, t).r;
-        fd[8] = trip(hi + 5 * RS, t).l;
-        if (!SIMPLE && rm.wall >= 0) zou_he<F2>(rm.wall, fd, ev(-0.5f * cur.Fx), ev(-0.5f * cur.Fy));
+        fd[1] = tripp(r2 + (R_F1 + 0) * RS).l;
+        fd[2] = f2cc;
+        fd[3] = tripp(r2 + (R_F1 + 1) * RS).r;
+        fd[4] = f4;
+        fd[5] = tripp(r0 + (R_F1 + 2) * RS).l;
+        fd[6] = tripp(r0 + (R_F1 + 3) * RS).r;
+        fd[7] = tripp(r1 + (R_F1 + 4) * RS).r;
+        fd[8] = tripp(r1 + (R_F1 + 5) * RS).l;
+        if (!SIMPLE && rm.wall >= 0) zou_he<F2>(rm.wall, fd, ev(-0.5f * Fxc), ev(-0.5f * Fyc));
         const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const F2 rho_new = P.rho_ref + delta;
-        const F2 T_old = ld2(rT + s4_3 * RS + c2);
-        F2 T_new = T_old;
-        if (ENERGY) {
-          const Trip tm = trip(mid + 6 * RS, t), tu = trip(hi + 6 * RS, t), td = trip(lo + 6 * RS, t);
-          const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
-          const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
-          const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * tm.c) +
-                         (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * tm.c);
-          const F2 adv = cur.ux * gtx + cur.uy * gty;
-          const F2 cond = cur.lam * lap + cur.gdx * gtx + cur.gdy * gty;
-          const F2 comp = T_dpdT(P, cur.A, cur.B, P.T_ref + tm.c) * cur.div;
-          const F2 k2 = ev((cond - comp) * cur.inv_rcv) - adv;
-          T_new = T_new + 0.5f * (cur.k1 + k2);
-          if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes keep their value
-            float tw;
-            const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
-            T_new = F2(d0 ? T_old.lo() : T_new.lo(), d1 ? T_old.hi() : T_new.hi());
-          }
-        }
-        const long long k = (long long)r * P.nx + gx0;
+        const long long k = (long long)r * P.nx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) st2(fout + i * plane + k, fd[i]);
-        st2(Tout + k, T_new);
+        if (!ENERGY) {
+          const F2 T_old = ld2(r2 + (R_T) * RS);
+          st2(Tout + k, T_old);
+          t_sum = t_sum + T_old;
+        }
         rho_min = fminf(rho_min, fminf(rho_new.lo(), rho_new.hi()));
-        t_sum = t_sum + T_new;
         const float wr = (!SIMPLE && any_outflow) ? (float)line_weight(r, P.ny, P.hbc[2], P.hbc[3]) : 1.0f;
         const F2 yk = wr * rho_new + acc_n;
         const F2 tk = acc_s + yk;
         acc_n = yk - (tk - acc_s);
         acc_s = tk;
       }
+      if (ENERGY) {
+        const Trip rmd = tripp(r2 + (R_RHO) * RS), tm = tripp(r2 + (R_T) * RS);
+        if (iq >= 4) {
+          if (!rm.solid) {
+            PairHeun &c = nxt;
+            const Trip ru = tripp(r1 + (R_RHO) * RS), tu = tripp(r1 + (R_T) * RS);
+            const F2 rho = rmd.c, T0 = tm.c;
+            const Trip xu = tripp(r1 + (R_UX) * RS), xm = tripp(r2 + (R_UX) * RS), xd = tripp(r0 + (R_UX) * RS);
+            const Trip yu = tripp(r1 + (R_UY) * RS), ym = tripp(r2 + (R_UY) * RS), yd = tripp(r0 + (R_UY) * RS);
+            const F2 ux = xm.c, uy = ym.c;
+            pr_parts(P, rho, &c.A, &c.B);
+            c.T0 = T0;
+            c.inv_rcv = irc * P.cv_inv;
+            c.lam = P.lam_v + P.dlam * (rho - P.rho_v);
+            // 9-point stencils; the lower row's share was formed when it was the centre
+            c.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l) + ld2(share + 0 * RS));
+            c.gdy = P.dlam * (third * ru.c + twelfth * (ru.r + ru.l) + ld2(share + 1 * RS));
+            c.div = third * (xm.r - xm.l) + twelfth * (xu.r - xu.l - xd.l + xd.r) + third * (yu.c - yd.c) +
+                    twelfth * (yu.r + yu.l - yd.l - yd.r);
+            F2 Ts;
+            if (!SIMPLE && rm.outflow) {
+              Ts = ld2(r0 + (R_TS) * RS);  // outflow row: copy of the first interior row
+              c.k1 = F2(0.0f);
+            } else {
+              const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l) + ld2(share + 2 * RS);
+              const F2 gty = third * tu.c + twelfth * (tu.r + tu.l) + ld2(share + 3 * RS);
+              const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l - 4.0f * T0) +
+                             (1.0f / 6.0f) * (tu.r + tu.l - 4.0f * T0) + ld2(share + 4 * RS);
+              // (lambda lap T + grad lambda . grad T - T (dp/dT) div u) / (rho c_v) - u . grad T
+              const F2 adv = ux * gtx + uy * gty;
+              const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
+              const F2 comp = T_dpdT(P, c.A, c.B, P.T_ref + T0) * c.div;
+              const F2 k1 = ev((cond - comp) * c.inv_rcv) - adv;
+              c.k1 = k1;
+              Ts = T0 + k1;
+              if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes of a boundary line
+                float tw0, tw1;
+                const bool d0 = t_fixed(P, col0, rm.src, &tw0), d1 = t_fixed(P, col1, rm.src, &tw1);
+                if (d0 || d1) {
+                  Ts = F2(d0 ? tw0 - P.T_ref : Ts.lo(), d1 ? tw1 - P.T_ref : Ts.hi());
+                  c.k1 = F2(d0 ? 0.0f : k1.lo(), d1 ? 0.0f : k1.hi());
+                }
+              }
+            }
+            st2(r2 + (R_TS) * RS, Ts);
+            if (!SIMPLE && r == 1 && P.hbc[2] == WALL) st2(r1 + (R_TS) * RS, Ts);  // mirror ghost of row -1
+          } else if (!SIMPLE && r == P.ny && P.hbc[3] == WALL) {
+            st2(r2 + (R_TS) * RS, ld2(r1 + (R_TS) * RS));  // mirror ghost of row ny
+          }
+        }
+        // this row's share of the stencils of the row above (used by the next iteration)
+        st2(share + 0 * RS, ev(twelfth * (rmd.r - rmd.l)));
+        st2(share + 1 * RS, -(third * rmd.c + twelfth * (rmd.l + rmd.r)));
+        st2(share + 2 * RS, ev(twelfth * (tm.r - tm.l)));
+        st2(share + 3 * RS, -(third * tm.c + twelfth * (tm.l + tm.r)));
+        st2(share + 4 * RS, (2.0f / 3.0f) * tm.c + (1.0f / 6.0f) * (tm.l + tm.r));
+        // the second Heun stage reads this iteration's T*, and the next first stage overwrites
+        // the rho and T ring rows read above
+        __syncthreads();
+      }
     }
-    c1jx = n1jx;
-    c1jy = n1jy;
-    cc2 = nn2;
-    cur = nxt;
+
+    // ---- S4: row q-3 (second Heun stage, store of T) ----
+    if (ENERGY && iq >= 6 && t_in) {
+      const int r = q - 3;
+      const LineMap rm = row_map(r);
+      if (!rm.outflow) {
+        const PairHeun &c = cur;
+        const Trip tm = tripp(r0 + (R_TS) * RS), tu = tripp(r2 + (R_TS) * RS), td = tripp(r1 + (R_TS) * RS);
+        const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
+        const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
+        const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * tm.c) +
+                       (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * tm.c);
+        // u of row q - 3 is still in its ring slot (overwritten by the next collision stage)
+        const F2 adv = ld2(r0 + (R_UX) * RS) * gtx + ld2(r0 + (R_UY) * RS) * gty;
+        const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
+        const F2 comp = T_dpdT(P, c.A, c.B, P.T_ref + tm.c) * c.div;
+        const F2 k2 = ev((cond - comp) * c.inv_rcv) - adv;
+        F2 T_new = c.T0 + 0.5f * (c.k1 + k2);
+        if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes keep their value
+          float tw;
+          const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
+          T_new = F2(d0 ? c.T0.lo() : T_new.lo(), d1 ? c.T0.hi() : T_new.hi());
+        }
+        st2(Tout + (long long)r * P.nx, T_new);
+        t_sum = t_sum + T_new;
+      }
+    }
+    // hand over to the next iteration: carried values by row, slot roles rotated
+    if (use_tma) ph ^= 1u << k0;
+    jc_x = jn_x;
+    jc_y = jn_y;
     f0c = f0n;
-    f2c2 = f2c1;
-    f2c1 = f2n;
-    f3 = f3 == 2 ? 0 : f3 + 1;
+    f2cc = f2c;
+    f2c = f2n;
+    Fxc = Fxn;
+    Fyc = Fyn;
+    irc = irn;
+    cur = nxt;
+    {
+      float *rt = r2;
+      r2 = r1;
+      r1 = r0;
+      r0 = rt;
+      const float *gt = g2;
+      g2 = g1;
+      g1 = g0;
+      g0 = gt;
+      const int kt = k2;
+      k2 = k1;
+      k1 = k0;
+      k0 = kt;
+    }
   }
   cp_async_wait<0>();
   double acc = ((double)acc_s.lo() + (double)acc_n.lo()) + ((double)acc_s.hi() + (double)acc_n.hi());
@@ -465,19 +525,20 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   if (!(rho_min > 0.0f)) flags |= FLAG_RHO_NONPOS;
   if (!isfinite(acc) || !isfinite((double)t_sum.lo() + (double)t_sum.hi())) flags |= FLAG_NAN;
   if (flags) atomicOr(io.status, flags);
-  block_mass_finalize<NT, false>(P, io, acc, 0.0);
+  tile_mass_finalize<NT, false>(P, io, acc, 0.0, bid, nblk, done, done_value);
 }
 
-template <bool ENERGY, int NT, int PF>
-__global__ void __launch_bounds__(NT, 320 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
+template <bool ENERGY, int NT>
+__global__ void __launch_bounds__(NT, 384 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned long long bars[PF + 3];  // mbarriers of the TMA staging slots
+  __shared__ unsigned long long bars[kPairSlots];  // mbarriers of the TMA staging slots
   const int ya = blockIdx.y * H;
   const int yb = min(ya + H, P.ny);
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
   if (ya - 3 >= 1 && yb + 2 <= P.ny - 2)
-    row_body_pair<ENERGY, NT, PF, true>(P, io, H, smem_raw, bars);
+    row_body_pair<ENERGY, NT, true>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
   else
-    row_body_pair<ENERGY, NT, PF, false>(P, io, H, smem_raw, bars);
+    row_body_pair<ENERGY, NT, false>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
 }
 
 }  // namespace ppl_dev

@@ -64,6 +64,8 @@ int cuda_err(cudaError_t e);
     if (_rc != PPL_OK) return _rc;              \
   } while (0)
 
+// checks a configuration (sizes, parameters, boundary combinations): PPL_OK or PPL_E_INVAL
+int validate(const ppl_config *c);
 // a state carrying d/d(sigma) or d/d(kappa) (FP64 or FP32)
 bool is_tangent(int prec);
 bool is_tangent32(int prec);

@@ -23,14 +23,14 @@ StepVariant step_variant_fp32() {
 
 template <bool ENERGY>
 static const void *fp32_pair_fn() {
-  return (const void *)row_step_pair<ENERGY, kNTP, kPFP>;
+  return (const void *)row_step_pair<ENERGY, kNTP>;
 }
 
 StepVariant step_variant_fp32_pair() {
   StepVariant v;
   v.nt = kNTP;
   v.width = 2 * kNTP - 8;
-  v.smem = row_step_pair_smem_bytes<kNTP, kPFP>();
+  v.smem = row_step_pair_smem_bytes<kNTP>();
   v.fn[0] = fp32_pair_fn<false>();
   v.fn[1] = fp32_pair_fn<true>();
   return v;

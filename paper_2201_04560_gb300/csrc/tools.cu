@@ -163,6 +163,18 @@ struct ppl_batch {
   std::vector<int> graph_energy[2];
   std::vector<uint64_t> graph_gen[2];  // shape_gen of each sim at capture
   int period = 1;  // outer steps per graph
+  // persistent mode: one launch for all meshes and outer steps (batch_persist.cu)
+  int mode = PPL_BATCH_GRAPH;
+  unsigned long long wait_ns = 1000000000ull;  // bound of every dependency wait
+  PersistMesh *h_meshes = nullptr;             // pinned staging of the mesh table
+  PersistMesh *d_meshes = nullptr;
+  PersistItem *d_items = nullptr;
+  void *d_ctl = nullptr;
+  unsigned *h_abort = nullptr;  // pinned copy of the abort word
+  int n_items = 0;
+  std::vector<uint64_t> items_gen;  // shape_gen of each sim when the item list was built
+  cudaGraphExec_t pgraph = nullptr;
+  int64_t pgraph_outer = -1;
 };
 
 namespace {
@@ -170,6 +182,12 @@ namespace {
 void batch_free(ppl_batch *b) {
   for (int i = 0; i < 2; ++i)
     if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+  if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+  if (b->h_meshes) cudaFreeHost(b->h_meshes);
+  if (b->h_abort) cudaFreeHost(b->h_abort);
+  cudaFree(b->d_meshes);
+  cudaFree(b->d_items);
+  cudaFree(b->d_ctl);
   for (auto s : b->branch) cudaStreamDestroy(s);
   for (auto e : b->done) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -231,6 +249,131 @@ int batch_capture(ppl_batch *b, const std::vector<int> &pat, cudaGraphExec_t *ou
   return PPL_OK;
 }
 
+// Every handle steps with the FP32 two-column kernel: the persistent mode applies.
+bool persistent_applicable(const ppl_batch *b) {
+  if (b->sims.size() > (size_t)kPersistMaxMeshes) return false;
+  for (auto h : b->sims)
+    if (h->prec != PPL_FP32DEV || h->var.fn[0] != step_variant_fp32_pair().fn[0]) return false;
+  return true;
+}
+
+// work items of one outer step: all tiles of a step together, steps ordered by their time
+// j / sub within the outer step (ties: the larger number of substeps first)
+std::vector<PersistItem> persistent_items(const ppl_batch *b) {
+  struct Key {
+    double t;
+    int sub, mesh, step;
+  };
+  std::vector<Key> keys;
+  for (size_t m = 0; m < b->sims.size(); ++m)
+    for (int j = 0; j < b->sub[m]; ++j) keys.push_back({(double)j / b->sub[m], b->sub[m], (int)m, j});
+  std::stable_sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) {
+    return x.t < y.t || (x.t == y.t && x.sub > y.sub);
+  });
+  std::vector<PersistItem> items;
+  for (const Key &k : keys) {
+    const ppl_sim *h = b->sims[k.mesh];
+    const int tiles = (int)(h->grid.x * h->grid.y);
+    for (int i = 0; i < tiles; ++i) items.push_back({k.mesh, k.step, i});
+  }
+  return items;
+}
+
+int persistent_step(ppl_batch *b, int64_t outer) {
+  if (!persistent_applicable(b)) return PPL_E_INVAL;
+  const int n = (int)b->sims.size();
+  if (!b->d_ctl) {
+    CK(cudaMallocHost((void **)&b->h_meshes, kPersistMaxMeshes * sizeof(PersistMesh)));
+    CK(cudaMallocHost((void **)&b->h_abort, sizeof(unsigned)));
+    CK(cudaMalloc((void **)&b->d_meshes, kPersistMaxMeshes * sizeof(PersistMesh)));
+    CK(cudaMalloc(&b->d_ctl, persistent_ctl_bytes()));
+  }
+  std::vector<uint64_t> gen;
+  for (auto h : b->sims) gen.push_back(h->shape_gen);
+  if (gen != b->items_gen || !b->d_items) {
+    std::vector<PersistItem> items = persistent_items(b);
+    CK(cudaStreamSynchronize(b->main));
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    CK(cudaMalloc((void **)&b->d_items, items.size() * sizeof(PersistItem)));
+    CK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(PersistItem), cudaMemcpyHostToDevice));
+    b->n_items = (int)items.size();
+    b->items_gen = gen;
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+    b->pgraph = nullptr;
+  }
+  // the mesh table of this launch (read by the graph's copy node when it runs)
+  CK(cudaStreamSynchronize(b->main));
+  for (int m = 0; m < n; ++m) {
+    ppl_sim *h = b->sims[m];
+    PersistMesh &M = b->h_meshes[m];
+    M.P = h->pf;
+    for (int i = 0; i < 2; ++i) {
+      M.f[i] = h->f[i];
+      M.T[i] = h->T[i];
+      M.stats[i] = h->stats[i];
+    }
+    M.partials = h->partials;
+    M.counter = h->counter;
+    M.status = h->status;
+    M.tmaps = h->tmaps;
+    M.gx = (int)h->grid.x;
+    M.gy = (int)h->grid.y;
+    M.H = h->rows_per_cta;
+    M.sub = b->sub[m];
+    M.cur0 = h->cur;
+    M.energy_on = h->cfg.energy_on;
+    M.step0 = h->step;
+    M.iso_steps = h->cfg.iso_steps;
+  }
+  if (!b->pgraph || b->pgraph_outer != outer) {
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+    b->pgraph = nullptr;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm = persistent_batch_ctas_per_sm();
+    if (per_sm < 1) return PPL_E_CUDA;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+    int rc = cuda_err(cudaMemcpyAsync(b->d_meshes, b->h_meshes, n * sizeof(PersistMesh), cudaMemcpyHostToDevice,
+                                      b->main));
+    if (rc == PPL_OK) rc = cuda_err(cudaMemsetAsync(b->d_ctl, 0, persistent_ctl_bytes(), b->main));
+    if (rc == PPL_OK)
+      rc = cuda_err(launch_persistent_batch(b->d_meshes, b->d_items, b->n_items, (int)outer, b->d_ctl, b->wait_ns,
+                                            sms * per_sm, b->main));
+    cudaError_t ce = cudaStreamEndCapture(b->main, &g);
+    if (rc != PPL_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CK(ce);
+    ce = cudaGraphInstantiate(&b->pgraph, g, 0);
+    cudaGraphDestroy(g);
+    CK(ce);
+    b->pgraph_outer = outer;
+  }
+  CK(cudaGraphLaunch(b->pgraph, b->main));
+  CK(cudaMemcpyAsync(b->h_abort, (const char *)b->d_ctl + sizeof(unsigned), sizeof(unsigned),
+                     cudaMemcpyDeviceToHost, b->main));
+  CK(cudaStreamSynchronize(b->main));
+  for (int m = 0; m < n; ++m) {
+    ppl_sim *h = b->sims[m];
+    const int64_t k = outer * b->sub[m];
+    h->step += k;
+    h->launches += k;
+    if (k & 1) h->cur = 1 - h->cur;
+  }
+  if (*b->h_abort) {
+    // a stopped launch leaves steps half done: clear each mesh's tile counter so that the
+    // handles can be reset or reloaded and stepped again
+    for (auto h : b->sims) CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned), b->main));
+    CK(cudaStreamSynchronize(b->main));
+    return PPL_E_TIMEOUT;
+  }
+  return PPL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -276,12 +419,41 @@ int ppl_batch_create(ppl_t *const *sims, const int32_t *substeps, int32_t n, ppl
   return PPL_OK;
 }
 
+int ppl_batch_set_mode(ppl_batch_t *b, int mode) {
+  if (!b || (mode != PPL_BATCH_GRAPH && mode != PPL_BATCH_PERSISTENT)) return PPL_E_INVAL;
+  if (mode == PPL_BATCH_PERSISTENT && !persistent_applicable(b)) return PPL_E_INVAL;
+  b->mode = mode;
+  return PPL_OK;
+}
+
+int ppl_batch_get_mode(const ppl_batch_t *b) { return b ? b->mode : PPL_E_INVAL; }
+
+int ppl_batch_set_wait_limit(ppl_batch_t *b, int64_t ns) {
+  if (!b || ns < 0) return PPL_E_INVAL;
+  b->wait_ns = (unsigned long long)ns;
+  if (b->pgraph) cudaGraphExecDestroy(b->pgraph);  // the limit is a kernel argument of the captured launch
+  b->pgraph = nullptr;
+  return PPL_OK;
+}
+
 int ppl_batch_step(ppl_batch_t *b, int64_t outer) {
   if (!b || outer < 0) return PPL_E_INVAL;
   // the batch stream starts after everything already queued on the sims' own streams
   for (auto h : b->sims) {
     CK(cudaEventRecord(b->fork, h->stream));
     CK(cudaStreamWaitEvent(b->main, b->fork, 0));
+  }
+  if (b->mode == PPL_BATCH_PERSISTENT && outer > 0) {
+    int prc = persistent_step(b, outer);
+    CK(cudaEventRecord(b->fork, b->main));
+    for (auto h : b->sims) CK(cudaStreamWaitEvent(h->stream, b->fork, 0));
+    if (prc != PPL_OK) return prc;
+    int rc = PPL_OK;
+    for (auto h : b->sims) {
+      const int r = check_status(h);
+      if (r != PPL_OK && rc == PPL_OK) rc = r;
+    }
+    return rc;
   }
   int64_t left = outer;
   while (left > 0) {

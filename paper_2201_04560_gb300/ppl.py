@@ -90,6 +90,18 @@ def load_library(build_if_missing: bool = True):
     L.ppl_fields_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int]
     L.ppl_populations.argtypes = [H, _PD]
+    L.ppl_state_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    L.ppl_state_device.restype = ctypes.c_int
+    L.ppl_snapshot_bytes.argtypes = [H]
+    L.ppl_snapshot_bytes.restype = ctypes.c_size_t
+    L.ppl_snapshot.argtypes = [H, ctypes.c_void_p]
+    L.ppl_snapshot.restype = ctypes.c_int
+    L.ppl_restore.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
+    L.ppl_restore.restype = ctypes.c_int
+    L.ppl_adjoint_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    L.ppl_adjoint_scratch_bytes.restype = ctypes.c_size_t
+    L.ppl_adjoint_step.argtypes = [ctypes.POINTER(PplConfig)] + [ctypes.c_void_p] * 7
+    L.ppl_adjoint_step.restype = ctypes.c_int
     L.ppl_tangent_fields.argtypes = [H, _PD, _PD, _PD, _PD]
     L.ppl_tangent_fields.restype = ctypes.c_int
     L.ppl_norms.argtypes = [H, ctypes.POINTER(PplNorms)]
@@ -122,6 +134,12 @@ def load_library(build_if_missing: bool = True):
     L.ppl_batch_step.argtypes = [H, ctypes.c_int64]
     L.ppl_batch_destroy.argtypes = [H]
     L.ppl_batch_destroy.restype = None
+    L.ppl_batch_set_mode.argtypes = [H, ctypes.c_int]
+    L.ppl_batch_set_mode.restype = ctypes.c_int
+    L.ppl_batch_get_mode.argtypes = [H]
+    L.ppl_batch_get_mode.restype = ctypes.c_int
+    L.ppl_batch_set_wait_limit.argtypes = [H, ctypes.c_int64]
+    L.ppl_batch_set_wait_limit.restype = ctypes.c_int
     L.ppl_set_launch.argtypes = [H, ctypes.c_int32]
     L.ppl_get_launch.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     L.ppl_autotune.argtypes = [H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _PD]
@@ -270,6 +288,20 @@ def step_noalloc(cfg: dict, f_in, T_in, f_out, T_out, stats_in, stats_out, statu
     return load_library().ppl_step_noalloc(ctypes.byref(C), *ptrs, ctypes.c_void_p(handle or None))
 
 
+def adjoint_scratch_bytes(nx: int, ny: int) -> int:
+    return int(load_library().ppl_adjoint_scratch_bytes(int(nx), int(ny)))
+
+
+def adjoint_step(cfg: dict, f, T, fbar_in, fbar_out, grad, scratch, stream=None):
+    """ppl_adjoint_step on device buffers (integer device addresses, e.g. torch data_ptr()s):
+    fbar_out = (d f^{n+1} / d f^n)^T fbar_in, grad[0:2] += d/d(sigma, kappa). Raises on error."""
+    C, keep = make_config(cfg)
+    handle = getattr(stream, "cuda_stream", stream)
+    ptrs = [ctypes.c_void_p(int(p)) for p in (f, T, fbar_in, fbar_out, grad, scratch)]
+    _check(load_library().ppl_adjoint_step(ctypes.byref(C), *ptrs, ctypes.c_void_p(handle or None)),
+           "ppl_adjoint_step")
+
+
 class Simulation:
     """One ppl handle: device-resident state advanced by the fused sm_103a step kernel."""
 
@@ -329,6 +361,24 @@ class Simulation:
         f = np.empty((9, self.ny, self.nx))
         _check(self.lib.ppl_populations(self.h, _ptr(f)), "ppl_populations")
         return f
+
+    def state_device(self, f, T):
+        """FP64 absolute populations [9][ny][nx] and T [ny][nx] of the current state into two
+        device buffers (integer addresses, e.g. torch data_ptr()s)."""
+        _check(self.lib.ppl_state_device(self.h, ctypes.c_void_p(int(f)), ctypes.c_void_p(int(T))),
+               "ppl_state_device")
+
+    @property
+    def snapshot_bytes(self) -> int:
+        return int(self.lib.ppl_snapshot_bytes(self.h))
+
+    def snapshot(self, dst):
+        """Copy the stored state into a device buffer of snapshot_bytes (async on the stream)."""
+        _check(self.lib.ppl_snapshot(self.h, ctypes.c_void_p(int(dst))), "ppl_snapshot")
+
+    def restore(self, src, step: int):
+        """Make a snapshot the current state, with the step counter set to `step`."""
+        _check(self.lib.ppl_restore(self.h, ctypes.c_void_p(int(src)), int(step)), "ppl_restore")
 
     def norms(self):
         n = PplNorms()
@@ -417,11 +467,16 @@ def cross_norm(coarse: Simulation, fine: Simulation, field: str = "rho"):
     return num.value, den.value
 
 
+BATCH_MODES = {"graph": 0, "persistent": 1}
+
+
 class Batch:
     """Handles advanced together, handle k by substeps[k] steps per outer step (Sec. 3:
-    dt ~ dx^2), their grids running concurrently as the branches of one CUDA graph."""
+    dt ~ dx^2). mode "graph": the grids run concurrently as the branches of one CUDA graph;
+    "persistent": one persistent launch (captured in a CUDA graph) takes the tiles of every
+    mesh's steps from a ticket counter (FP32 two-column handles only)."""
 
-    def __init__(self, sims, substeps):
+    def __init__(self, sims, substeps, mode: str = "graph"):
         if len(sims) != len(substeps):
             raise ValueError("one substep count per simulation")
         self.lib = load_library()
@@ -430,6 +485,19 @@ class Batch:
         subs = (ctypes.c_int32 * len(sims))(*[int(k) for k in substeps])
         self.b = ctypes.c_void_p()
         _check(self.lib.ppl_batch_create(hs, subs, len(sims), ctypes.byref(self.b)), "ppl_batch_create")
+        if mode != "graph":
+            self.set_mode(mode)
+
+    def set_mode(self, mode: str):
+        _check(self.lib.ppl_batch_set_mode(self.b, BATCH_MODES[mode]), "ppl_batch_set_mode")
+
+    @property
+    def mode(self) -> str:
+        return {v: k for k, v in BATCH_MODES.items()}[int(self.lib.ppl_batch_get_mode(self.b))]
+
+    def set_wait_limit(self, ns: int):
+        """Bound of every dependency wait of the persistent launch, in nanoseconds."""
+        _check(self.lib.ppl_batch_set_wait_limit(self.b, int(ns)), "ppl_batch_set_wait_limit")
 
     def step(self, outer: int = 1):
         _check(self.lib.ppl_batch_step(self.b, int(outer)), "ppl_batch_step")

@@ -426,9 +426,10 @@ def fp32_error_study(steps_scale=1.0):
 
 
 def batch_throughput(meshes=(128, 256, 512), outer=200, precision="fp32", autotune_steps=64):
-    """The batched refinement sequence (concurrent graph branches) against stepping the same
-    handles one after another: wall time of `outer` outer steps (1 : 4 : 16 steps per coarse
-    step for 128^2 / 256^2 / 512^2) each way, from the same initial states."""
+    """The batched refinement sequence against stepping the same handles one after another:
+    wall time of `outer` outer steps (1 : 4 : 16 steps per coarse step for 128^2 / 256^2 /
+    512^2) each way, from the same initial states; the batch both as concurrent graph
+    branches and as one persistent launch (FP32 two-column handles)."""
     base_n = meshes[0]
     Tc, rv, rl = coexistence(0.8)
     sigma = ppl.sigma_for(EOS["a"], EOS["b"], EOS["R"], EOS["omega"], EOS["G"], 0.8 * Tc)
@@ -445,9 +446,12 @@ def batch_throughput(meshes=(128, 256, 512), outer=200, precision="fp32", autotu
             s = ppl.Simulation(c, *ic)
             if autotune_steps:
                 s.autotune(autotune_steps)
+                if mode == "persistent" and s.kernel != "pair":
+                    s.select_kernel("pair")  # the persistent launch runs the two-column kernel
             sims.append(s)
         return sims
 
+    mode = "graph"
     sims = make()
     for s, k in zip(sims, subs):  # warm-up (graph capture)
         s.step(2 * k)
@@ -457,14 +461,22 @@ def batch_throughput(meshes=(128, 256, 512), outer=200, precision="fp32", autotu
     seq = time.perf_counter() - t0
     for s in sims:
         s.close()
-    sims = make()
-    with ppl.Batch(sims, subs) as b:
-        b.step(2)
-        t0 = time.perf_counter()
-        b.step(outer)
-        bat = time.perf_counter() - t0
-    for s in sims:
-        s.close()
+    times = {}
+    for mode in ("graph", "persistent") if precision == "fp32" else ("graph",):
+        sims = make()
+        with ppl.Batch(sims, subs, mode=mode) as b:
+            b.step(2)
+            if mode == "persistent":
+                b.step(outer)  # capture of the launch for this outer count
+            t0 = time.perf_counter()
+            b.step(outer)
+            times[mode] = time.perf_counter() - t0
+        for s in sims:
+            s.close()
+    bat = times["graph"]
     nodes = sum(n * n * k for n, k in zip(meshes, subs)) * outer
-    return {"meshes": list(meshes), "substeps": subs, "outer": outer, "sequential_s": seq, "batch_s": bat,
-            "speedup": seq / bat, "batch_mlups": nodes / bat / 1e6, "sequential_mlups": nodes / seq / 1e6}
+    out = {"meshes": list(meshes), "substeps": subs, "outer": outer, "sequential_s": seq, "batch_s": bat,
+           "speedup": seq / bat, "batch_mlups": nodes / bat / 1e6, "sequential_mlups": nodes / seq / 1e6}
+    if "persistent" in times:
+        out.update(persistent_s=times["persistent"], persistent_mlups=nodes / times["persistent"] / 1e6)
+    return out

@@ -239,3 +239,73 @@ def test_wall_heat_flux_matches_oracle(ppl, th, precision, rtol):
     with pytest.raises(ppl.PplError):
         s.wall_heat_flux(0)  # periodic side
     s.close()
+
+
+def _sequence_fp32(ppl, th, ns):
+    base, _ = droplet(th, ns[0], precision="fp32", kappa=0.2)
+    base.update(gy=-2e-5, energy_on=1, iso_steps=5, cv=6.0, lambda_l=0.2, lambda_v=0.2)
+    cfgs, ics = [], []
+    for n in ns:
+        c = ppl.refine(base, ns[0], n, 0.8)
+        c.update(precision="fp32")
+        cfgs.append(c)
+        _, icn = droplet(th, n, precision="fp32")
+        rho, ux, uy, _ = icn
+        ics.append((rho, ux, uy, np.full_like(rho, c["T_ref"])))
+    return cfgs, ics
+
+
+@pytest.mark.parametrize("ns,subs,outer", [((24, 48, 96), (1, 4, 16), 3), ((64, 128, 256), (1, 4, 16), 2),
+                                           ((32, 48, 64), (1, 2, 3), 5)])
+def test_persistent_batch_equals_separate_handles(ppl, th, ns, subs, outer):
+    # one persistent launch per call over every mesh's steps (gravity: each step waits for
+    # its mesh's domain-mean density; the energy equation switches on during the run); the
+    # separately stepped 256^2 handle stages rows by TMA, the batch by per-thread copies
+    cfgs, ics = _sequence_fp32(ppl, th, ns)
+    sims = [ppl.Simulation(c, *ic) for c, ic in zip(cfgs, ics)]
+    with ppl.Batch(sims, subs, mode="persistent") as b:
+        assert b.mode == "persistent"
+        b.step(outer)
+        b.step(1)
+    for k, (c, ic) in enumerate(zip(cfgs, ics)):
+        ref = ppl.Simulation(c, *ic)
+        ref.step((outer + 1) * subs[k])
+        np.testing.assert_array_equal(sims[k].populations(), ref.populations())
+        np.testing.assert_array_equal(sims[k].fields()["T"], ref.fields()["T"])
+        assert sims[k].norms()["mass"] == ref.norms()["mass"]
+        assert sims[k].launch_count == ref.launch_count == (outer + 1) * subs[k]
+        ref.close()
+        sims[k].step(3)  # the handle keeps stepping on its own
+        sims[k].close()
+
+
+def test_persistent_batch_wait_limit_runs_out(ppl, th):
+    # a zero wait limit makes the first dependency wait give up: the launch stops, the call
+    # reports PPL_E_TIMEOUT, nothing faults, and the handles step normally after a reset
+    cfgs, ics = _sequence_fp32(ppl, th, (64, 128, 256))
+    sims = [ppl.Simulation(c, *ic) for c, ic in zip(cfgs, ics)]
+    b = ppl.Batch(sims, (1, 4, 16), mode="persistent")
+    b.set_wait_limit(0)
+    with pytest.raises(ppl.PplError) as err:
+        b.step(2)
+    assert err.value.code == ppl.PPL_E_TIMEOUT
+    b.set_wait_limit(1_000_000_000)
+    for s, ic in zip(sims, ics):
+        s.reset(*ic)
+    b.step(1)
+    for s in sims:
+        assert s.norms()["flags"] == 0
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def test_persistent_batch_needs_two_column_fp32_handles(ppl, th):
+    c, ic = droplet(th, 24)  # FP64
+    s = ppl.Simulation(c, *ic)
+    b = ppl.Batch([s], [1])
+    with pytest.raises(ppl.PplError):
+        b.set_mode("persistent")
+    assert b.mode == "graph"
+    b.close()
+    s.close()
