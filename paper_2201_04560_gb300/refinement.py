@@ -381,6 +381,17 @@ def fp32_error_study(steps_scale=1.0):
             r[f + "_maxrel"] = float(np.max(np.abs(a[f] - b[f]) / np.abs(b[f])))
         r["rho_min_rel"] = float(abs(a["rho"].min() - b["rho"].min()) / b["rho"].min())
         r["rho_max_rel"] = float(abs(a["rho"].max() - b["rho"].max()) / b["rho"].max())
+        # pointwise in the bulk phases: nodes 8 or more nodes from every interface node
+        rho = b["rho"]
+        gap = float(rho.max() - rho.min())
+        near = (rho > rho.min() + 0.1 * gap) & (rho < rho.max() - 0.1 * gap)
+        for ax in (0, 1):
+            grown = near.copy()
+            for k in range(1, 9):
+                grown |= np.roll(near, k, axis=ax) | np.roll(near, -k, axis=ax)
+            near = grown
+        e = np.abs(a["rho"] - rho) / rho
+        r["rho_bulk_maxrel"] = float(e[~near].max()) if (~near).any() else float("nan")
         if extra:
             r.update(extra(res))
         return r
@@ -418,10 +429,30 @@ def fp32_error_study(steps_scale=1.0):
         return {"radius_max_rel": float(np.max(np.abs(a - b) / b)), "radius_final": float(b[-1])}
 
     out["droplet_vaporization_256"] = compare(pair(cfg, ic, n(20000), radius, n(1000)), radius_err)
-    # pool boiling (1024 x 2048)
+    # pool boiling (1024 x 2048): the vapour area over the heater (where the bubbles form) and
+    # the pool's free-surface height as the interface measures
     _, rv, rl = coexistence(0.86)
     cfg, ic = W.pool_boiling(Tc, rv, rl, sigma, nx=1024, ny=2048)
-    out["pool_boiling_1024x2048"] = compare(pair(cfg, ic, n(2000)))
+    midp, bandp = 0.5 * (rv + rl), 0.05 * (rl - rv)
+
+    def pool_measures(s):
+        rho = s.fields()["rho"]
+        frac = np.clip((rho - (midp - bandp)) / (2 * bandp), 0.0, 1.0)
+        nx = rho.shape[1]
+        heater = slice((nx - nx // 5) // 2, (nx + nx // 5) // 2)
+        vapour_heater = float((1.0 - frac[: rho.shape[0] // 3, heater]).sum())
+        col = frac.mean(axis=1)  # liquid fraction per row: the surface is where it falls through 1/2
+        i = int(np.argmax(col < 0.5))
+        surface = float(i - 1 + (col[i - 1] - 0.5) / (col[i - 1] - col[i])) if i > 0 else float("nan")
+        return vapour_heater, surface
+
+    def pool_err(res):
+        a, b = res["fp32"][1][-1], res["fp64"][1][-1]
+        return {"vapour_area_over_heater_rel": abs(a[0] - b[0]) / max(b[0], 1e-300),
+                "vapour_area_over_heater": b[0], "surface_height_abs_nodes": abs(a[1] - b[1]),
+                "surface_height": b[1]}
+
+    out["pool_boiling_1024x2048"] = compare(pair(cfg, ic, n(2000), pool_measures, n(2000)), pool_err)
     return out
 
 

@@ -323,3 +323,27 @@ def test_pair_kernel_wall_rows_fp32(sim_cls, th, case):
     for k in ("rho", "T"):
         assert l1rel(got[k], w[k]) <= 1e-4
         np.testing.assert_allclose(got[k], ref[k], rtol=5e-5, atol=5e-5 * np.abs(ref[k]).max())
+
+
+def test_stefan_strip_50000_steps_against_oracle(sim_cls, th):
+    # the Stefan strip at its workload size and length (1024 x 4, 50,000 steps; the oracle
+    # takes about 80 s of one host core): the FP64 step against the FP64 oracle, and the FP32
+    # step against the oracle in the L1 form of the FP32 budget
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.stefan_strip(e.Tc, rv, rl, th["sigma086"], nx=1024, ny=4, n_vapour=10)
+    steps = 50000
+    ref = oracle.Oracle(cfg, *ic)
+    ref.step(steps)
+    want = ref.fields()
+    for prec in ("fp64", "fp32"):
+        sim = sim_cls(dict(cfg, precision=prec), *ic)
+        sim.step(steps)
+        got = sim.fields()
+        sim.close()
+        if prec == "fp64":
+            assert rel(got["rho"], want["rho"]) <= FP64_RTOL
+            assert rel(got["T"], want["T"]) <= FP64_RTOL
+        else:
+            assert l1rel(got["rho"], want["rho"]) <= 1e-4
+            assert l1rel(got["T"], want["T"]) <= 1e-4
