@@ -369,7 +369,7 @@ int ppl_batch_step(ppl_batch_t *b, int64_t outer);
 void ppl_batch_destroy(ppl_batch_t *b);
 
 /* How a batch runs its outer steps (Sec. 3 refinement sequence, dt ~ dx^2).
- * PPL_BATCH_GRAPH (the default): one CUDA graph per outer step whose concurrent branches
+ * PPL_BATCH_GRAPH: one CUDA graph per outer step whose concurrent branches
  * launch each handle's steps. PPL_BATCH_PERSISTENT: one persistent launch per ppl_batch_step
  * call, captured in a CUDA graph, for handles that all step with the FP32 two-column kernel
  * (PPL_E_INVAL otherwise): resident CTAs take the tiles of every mesh's steps in time order
@@ -381,6 +381,7 @@ void ppl_batch_destroy(ppl_batch_t *b);
  * (ppl_reset or ppl_load them). ppl_launch_count counts the steps a handle made. */
 #define PPL_BATCH_GRAPH 0
 #define PPL_BATCH_PERSISTENT 1
+#define PPL_BATCH_AUTO 2 /* the default: persistent where it applies and no handle has gravity, else graph */
 int ppl_batch_set_mode(ppl_batch_t *b, int mode);
 int ppl_batch_get_mode(const ppl_batch_t *b);
 int ppl_batch_set_wait_limit(ppl_batch_t *b, int64_t ns);

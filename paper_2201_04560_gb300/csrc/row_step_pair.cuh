@@ -132,11 +132,12 @@ struct PairHeun {
 
 // One tile of the step: strip bx (2 NT - 8 interior columns) and row block by (H rows), CTA
 // bid of nblk for the mass reduction; `done` as in tile_mass_finalize.
+// reduce = false skips the mass reduction (a step whose domain mean nobody reads).
 template <bool ENERGY, int NT, bool SIMPLE>
 __device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int H, int bx, int by,
                                               unsigned bid, unsigned nblk, unsigned char *smem_raw,
                                               unsigned long long *bars, unsigned *done = nullptr,
-                                              unsigned done_value = 0) {
+                                              unsigned done_value = 0, bool reduce = true) {
   constexpr int SW = 2 * NT;  // strip columns
   constexpr int W = SW - 8;   // interior columns
   static_assert(W % 4 == 0, "strip starts must stay 16-byte aligned for the TMA copies");
@@ -525,7 +526,10 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   if (!(rho_min > 0.0f)) flags |= FLAG_RHO_NONPOS;
   if (!isfinite(acc) || !isfinite((double)t_sum.lo() + (double)t_sum.hi())) flags |= FLAG_NAN;
   if (flags) atomicOr(io.status, flags);
-  tile_mass_finalize<NT, false>(P, io, acc, 0.0, bid, nblk, done, done_value);
+  if (reduce)
+    tile_mass_finalize<NT, false>(P, io, acc, 0.0, bid, nblk, done, done_value);
+  else
+    __syncthreads();  // every thread's stores of this tile precede what the caller does next
 }
 
 template <bool ENERGY, int NT>

@@ -51,12 +51,16 @@ struct PersistMesh {
   int cur0;             // buffer holding the state at launch
   int energy_on;
   long long step0, iso_steps;
+  // no gravity: no step reads the domain mean, so a tile depends only on the tiles within the
+  // step's reach (one strip, reach_y row blocks each way) of the previous step
+  int local, reach_y, periodic_y;
+  int tile0;            // first of this mesh's per-tile step counters in the control block
 };
 struct PersistItem {  // one tile of one step of one mesh within an outer step
   int mesh, step, tile;
 };
 size_t persistent_batch_smem();
-size_t persistent_ctl_bytes();
+size_t persistent_ctl_bytes(int tiles);  // control block with per-tile counters for `tiles` tiles
 int persistent_batch_ctas_per_sm();
 // n_outer outer steps of every mesh: items (n_items per outer step) handed out in order
 cudaError_t launch_persistent_batch(const PersistMesh *meshes, const PersistItem *items, int n_items, int n_outer,

@@ -164,12 +164,13 @@ struct ppl_batch {
   std::vector<uint64_t> graph_gen[2];  // shape_gen of each sim at capture
   int period = 1;  // outer steps per graph
   // persistent mode: one launch for all meshes and outer steps (batch_persist.cu)
-  int mode = PPL_BATCH_GRAPH;
+  int mode = PPL_BATCH_AUTO;
   unsigned long long wait_ns = 1000000000ull;  // bound of every dependency wait
   PersistMesh *h_meshes = nullptr;             // pinned staging of the mesh table
   PersistMesh *d_meshes = nullptr;
   PersistItem *d_items = nullptr;
   void *d_ctl = nullptr;
+  size_t ctl_bytes = 0;
   unsigned *h_abort = nullptr;  // pinned copy of the abort word
   int n_items = 0;
   std::vector<uint64_t> items_gen;  // shape_gen of each sim when the item list was built
@@ -282,15 +283,23 @@ std::vector<PersistItem> persistent_items(const ppl_batch *b) {
 int persistent_step(ppl_batch *b, int64_t outer) {
   if (!persistent_applicable(b)) return PPL_E_INVAL;
   const int n = (int)b->sims.size();
-  if (!b->d_ctl) {
+  if (!b->h_meshes) {
     CK(cudaMallocHost((void **)&b->h_meshes, kPersistMaxMeshes * sizeof(PersistMesh)));
     CK(cudaMallocHost((void **)&b->h_abort, sizeof(unsigned)));
     CK(cudaMalloc((void **)&b->d_meshes, kPersistMaxMeshes * sizeof(PersistMesh)));
-    CK(cudaMalloc(&b->d_ctl, persistent_ctl_bytes()));
   }
   std::vector<uint64_t> gen;
-  for (auto h : b->sims) gen.push_back(h->shape_gen);
+  int tiles = 0;
+  for (auto h : b->sims) {
+    gen.push_back(h->shape_gen);
+    tiles += (int)(h->grid.x * h->grid.y);
+  }
   if (gen != b->items_gen || !b->d_items) {
+    CK(cudaStreamSynchronize(b->main));
+    cudaFree(b->d_ctl);
+    b->d_ctl = nullptr;
+    CK(cudaMalloc(&b->d_ctl, persistent_ctl_bytes(tiles)));
+    b->ctl_bytes = persistent_ctl_bytes(tiles);
     std::vector<PersistItem> items = persistent_items(b);
     CK(cudaStreamSynchronize(b->main));
     cudaFree(b->d_items);
@@ -304,9 +313,15 @@ int persistent_step(ppl_batch *b, int64_t outer) {
   }
   // the mesh table of this launch (read by the graph's copy node when it runs)
   CK(cudaStreamSynchronize(b->main));
+  int tile0 = 0;
   for (int m = 0; m < n; ++m) {
     ppl_sim *h = b->sims[m];
     PersistMesh &M = b->h_meshes[m];
+    M.local = h->cfg.gx == 0.0 && h->cfg.gy == 0.0;
+    M.reach_y = (3 + h->rows_per_cta - 1) / h->rows_per_cta;  // rows of the halo, in row blocks
+    M.periodic_y = h->cfg.hydro_bc[2] == PPL_PERIODIC;
+    M.tile0 = tile0;
+    tile0 += (int)(h->grid.x * h->grid.y);
     M.P = h->pf;
     for (int i = 0; i < 2; ++i) {
       M.f[i] = h->f[i];
@@ -338,7 +353,7 @@ int persistent_step(ppl_batch *b, int64_t outer) {
     CK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
     int rc = cuda_err(cudaMemcpyAsync(b->d_meshes, b->h_meshes, n * sizeof(PersistMesh), cudaMemcpyHostToDevice,
                                       b->main));
-    if (rc == PPL_OK) rc = cuda_err(cudaMemsetAsync(b->d_ctl, 0, persistent_ctl_bytes(), b->main));
+    if (rc == PPL_OK) rc = cuda_err(cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, b->main));
     if (rc == PPL_OK)
       rc = cuda_err(launch_persistent_batch(b->d_meshes, b->d_items, b->n_items, (int)outer, b->d_ctl, b->wait_ns,
                                             sms * per_sm, b->main));
@@ -420,7 +435,7 @@ int ppl_batch_create(ppl_t *const *sims, const int32_t *substeps, int32_t n, ppl
 }
 
 int ppl_batch_set_mode(ppl_batch_t *b, int mode) {
-  if (!b || (mode != PPL_BATCH_GRAPH && mode != PPL_BATCH_PERSISTENT)) return PPL_E_INVAL;
+  if (!b || (mode != PPL_BATCH_GRAPH && mode != PPL_BATCH_PERSISTENT && mode != PPL_BATCH_AUTO)) return PPL_E_INVAL;
   if (mode == PPL_BATCH_PERSISTENT && !persistent_applicable(b)) return PPL_E_INVAL;
   b->mode = mode;
   return PPL_OK;
@@ -443,7 +458,14 @@ int ppl_batch_step(ppl_batch_t *b, int64_t outer) {
     CK(cudaEventRecord(b->fork, h->stream));
     CK(cudaStreamWaitEvent(b->main, b->fork, 0));
   }
-  if (b->mode == PPL_BATCH_PERSISTENT && outer > 0) {
+  bool persistent = b->mode == PPL_BATCH_PERSISTENT;
+  if (b->mode == PPL_BATCH_AUTO) {
+    // the persistent launch where it applies and every mesh is free of gravity (tiles then
+    // wait only for their neighbours: measured faster than the graph branches); else graphs
+    persistent = persistent_applicable(b);
+    for (auto h : b->sims) persistent = persistent && h->cfg.gx == 0.0 && h->cfg.gy == 0.0;
+  }
+  if (persistent && outer > 0) {
     int prc = persistent_step(b, outer);
     CK(cudaEventRecord(b->fork, b->main));
     for (auto h : b->sims) CK(cudaStreamWaitEvent(h->stream, b->fork, 0));

@@ -467,16 +467,17 @@ def cross_norm(coarse: Simulation, fine: Simulation, field: str = "rho"):
     return num.value, den.value
 
 
-BATCH_MODES = {"graph": 0, "persistent": 1}
+BATCH_MODES = {"graph": 0, "persistent": 1, "auto": 2}
 
 
 class Batch:
     """Handles advanced together, handle k by substeps[k] steps per outer step (Sec. 3:
     dt ~ dx^2). mode "graph": the grids run concurrently as the branches of one CUDA graph;
     "persistent": one persistent launch (captured in a CUDA graph) takes the tiles of every
-    mesh's steps from a ticket counter (FP32 two-column handles only)."""
+    mesh's steps from a ticket counter (FP32 two-column handles only); "auto" (default): the
+    persistent launch where it applies and no handle has gravity, else the graph."""
 
-    def __init__(self, sims, substeps, mode: str = "graph"):
+    def __init__(self, sims, substeps, mode: str = "auto"):
         if len(sims) != len(substeps):
             raise ValueError("one substep count per simulation")
         self.lib = load_library()
@@ -485,7 +486,7 @@ class Batch:
         subs = (ctypes.c_int32 * len(sims))(*[int(k) for k in substeps])
         self.b = ctypes.c_void_p()
         _check(self.lib.ppl_batch_create(hs, subs, len(sims), ctypes.byref(self.b)), "ppl_batch_create")
-        if mode != "graph":
+        if mode != "auto":
             self.set_mode(mode)
 
     def set_mode(self, mode: str):
