@@ -6,9 +6,11 @@
 // (2t, 2t + 1) of a strip of 2 NT columns: 4 halo columns on each side, 2 NT - 8 interior
 // columns. Both columns of a thread are computed by one packed instruction wherever the
 // arithmetic allows (F2 in lane2.cuh), the staged rows and the stores move 8 bytes per
-// thread, and a column's neighbours come from one 8-byte and two 4-byte shared-memory
-// reads per pair (ring rows carry two zeroed pad floats on each side, so the reads of the
-// strip's outermost threads need no clamping: those columns are halo, never stored). With
+// thread. Ring rows keep the even columns in one half and the odd columns in the other, so
+// that each of a column pair's neighbour pairs (2t - 1, 2t), (2t, 2t + 1), (2t + 1, 2t + 2)
+// is two conflict-free 4-byte reads straight into a register pair (each half carries a
+// zeroed pad float at both ends, so the reads of the strip's outermost threads need no
+// clamping: those columns are halo, never stored). With
 // x periodic and nx even, a pair never straddles the domain edge and its global address is
 // 8-byte aligned. Rows (walls, outflow, Dirichlet lines in y) are handled as in the
 // one-column kernel; only per-node boundary data of a wall row (rho_w, T_w, the Dirichlet
@@ -44,21 +46,23 @@
 
 namespace ppl_dev {
 
-// values of the columns (2t - 1, 2t), (2t, 2t + 1), (2t + 1, 2t + 2) of one padded ring row
+// the pairs of columns (2t - 1, 2t), (2t, 2t + 1), (2t + 1, 2t + 2) around a thread's own pair
 struct Trip {
   F2 l, c, r;
 };
-__device__ __forceinline__ Trip trip(const float *row, int t) {
-  const float2 c = *reinterpret_cast<const float2 *>(row + 2 * t);
-  const float l = row[2 * t - 1], r = row[2 * t + 2];
-  return {F2(l, c.x), F2(c), F2(c.y, r)};
-}
-// the same three pairs, from a pointer already at the thread's column 2t
-__device__ __forceinline__ Trip tripp(const float *p) {
-  const float2 c = *reinterpret_cast<const float2 *>(p);
-  return {F2(p[-1], c.x), F2(c), F2(c.y, p[2])};
-}
 __device__ __forceinline__ F2 ld2(const float *p) { return F2(*reinterpret_cast<const float2 *>(p)); }
+// a ring row holds [pad, E_0 .. E_{NT-1}, pad, pad, O_0 .. O_{NT-1}, pad] with E_t, O_t the
+// columns 2t, 2t + 1; a thread's pointer addresses its E_t, and O_t lies NT + 2 floats further
+template <int NT>
+__device__ __forceinline__ F2 rld(const float *p) { return F2(p[0], p[NT + 2]); }
+template <int NT>
+__device__ __forceinline__ void rst(float *p, F2 v) { p[0] = v.lo(); p[NT + 2] = v.hi(); }
+template <int NT>
+__device__ __forceinline__ Trip rtrip(const float *p) {
+  const float e = p[0], o = p[NT + 2];
+  return {F2(p[NT + 1], e), F2(e, o), F2(o, p[1])};
+}
+
 __device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<float2 *>(p) = v.v; }
 __device__ __forceinline__ void cp_async8(float *smem_dst, const float *gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -154,7 +158,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   // shares of the stencils of the first Heun stage that the row below the centre contributes
   // (grad rho x, y; grad T x, y; Laplacian of T), formed when that row was the centre; each
   // thread reads back only its own columns
-  float *share = rings + kPairSlots * kPairRingRows * RS + 2 + 2 * threadIdx.x;
+  float *share = rings + kPairSlots * kPairRingRows * RS + 1 + threadIdx.x;
   enum { R_PSI = 0, R_RHO = 1, R_T = 2, R_UX = 3, R_UY = 4, R_F1 = 5, R_TS = 11 };
   const float third = 1.0f / 3.0f, twelfth = 1.0f / 12.0f;
   const float big = 3.0e38f;
@@ -207,7 +211,10 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
     tmap_acquire(io.tmap_f);
     tmap_acquire(io.tmap_T);
   }
-  for (int i = t; i < NRING * 4; i += NT) rings[(i >> 2) * RS + ((i & 3) < 2 ? (i & 3) : SW + (i & 3))] = 0.0f;
+  for (int i = t; i < NRING * 4; i += NT) {
+    const int k = i & 3;
+    rings[(i >> 2) * RS + (k == 0 ? 0 : k == 1 ? NT + 1 : k == 2 ? NT + 2 : 2 * NT + 3)] = 0.0f;
+  }
   __syncthreads();
   // row q into staging slot `slot` (TMA, one thread), or into this thread's columns at dst
   auto stage_row = [&](int q, int slot, const float *dst_c) {
@@ -230,8 +237,8 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
 
   // Slot roles: 0 holds rows q and q - 3, 1 rows q - 1 and q - 4, 2 rows q - 2 and q + 1.
   // Each iteration rotates the roles (0, 1, 2) <- (2, 0, 1).
-  float *r0 = rings + 0 * kPairRingRows * RS + 2 + c2, *r1 = rings + 2 * kPairRingRows * RS + 2 + c2,
-        *r2 = rings + 1 * kPairRingRows * RS + 2 + c2;
+  float *r0 = rings + 0 * kPairRingRows * RS + 1 + t, *r1 = rings + 2 * kPairRingRows * RS + 1 + t,
+        *r2 = rings + 1 * kPairRingRows * RS + 1 + t;
   const float *g0 = stg + 0 * 10 * SW + c2, *g1 = stg + 2 * 10 * SW + c2, *g2 = stg + 1 * 10 * SW + c2;
   int k0 = 0, k1 = 2, k2 = 1;  // slot numbers of the roles (TMA destination, mbarrier)
   unsigned ph = 0;              // mbarrier parity per slot (bit k)
@@ -269,9 +276,9 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         arg_min = fminf(arg_min, fminf(arg.lo(), arg.hi()));
         psi = sqrt(fmax(arg, F2(0.0f)));
       }
-      st2(r0 + (R_PSI) * RS, psi);
-      st2(r0 + (R_RHO) * RS, rho);
-      st2(r0 + (R_T) * RS, Tt);
+      rst<NT>(r0 + (R_PSI) * RS, psi);
+      rst<NT>(r0 + (R_RHO) * RS, rho);
+      rst<NT>(r0 + (R_T) * RS, Tt);
       const F2 d57 = f[5] - f[7], d68 = f[6] - f[8];
       jn_x = (f[1] - f[3]) + (d57 - d68);
       jn_y = (f[2] - f[4]) + (d57 + d68);
@@ -296,7 +303,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       const int r = q - 1;
       const LineMap rm = row_map(r);
       if (!rm.solid) {
-        const Trip pu = tripp(r0 + (R_PSI) * RS), pm = tripp(r1 + (R_PSI) * RS), pd = tripp(r2 + (R_PSI) * RS);
+        const Trip pu = rtrip<NT>(r0 + (R_PSI) * RS), pm = rtrip<NT>(r1 + (R_PSI) * RS), pd = rtrip<NT>(r2 + (R_PSI) * RS);
         const F2 p1 = pm.r, p3 = pm.l, p2 = pu.c, p4 = pd.c, p5 = pu.r, p6 = pu.l, p7 = pd.l, p8 = pd.r;
         const F2 psi_c = pm.c;
         const F2 d57 = p5 - p7, d86 = p8 - p6, s57 = p5 + p7, s68 = p6 + p8, s13 = p1 + p3, s24 = p2 + p4;
@@ -315,7 +322,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
             pf = P.Gw_over_G * psi_c;
             pq = psi_c;
           } else {
-            const F2 Tw = P.T_ref + ld2(r1 + (R_T) * RS);
+            const F2 Tw = P.T_ref + rld<NT>(r1 + (R_T) * RS);
             const float a0 = psi_arg(P, wall_rho_w(P, ws, col0, rm.src), Tw.lo());
             const float a1 = psi_arg(P, wall_rho_w(P, ws, col1, rm.src), Tw.hi());
             if (!(a0 >= 0.0f) || !(a1 >= 0.0f)) flags |= FLAG_PSI_NEG;
@@ -328,18 +335,18 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           qd = qd - third * pq;
         }
         const F2 qf = P.kappa_G2 * psi_c;
-        const F2 rho = ld2(r1 + (R_RHO) * RS);
+        const F2 rho = rld<NT>(r1 + (R_RHO) * RS);
         const F2 gps = (-P.G) * psi_c;
         const F2 fmx = gps * sx, fmy = gps * sy;
         const F2 Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
         const F2 inv_rho = 1.0f / rho;
         const F2 ux = (jc_x + 0.5f * Fx) * inv_rho;
         const F2 uy = (jc_y + 0.5f * Fy) * inv_rho;
-        st2(r1 + (R_UX) * RS, ux);
-        st2(r1 + (R_UY) * RS, uy);
+        rst<NT>(r1 + (R_UX) * RS, ux);
+        rst<NT>(r1 + (R_UY) * RS, uy);
         if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1 (slot of row q - 3)
-          st2(r0 + (R_UX) * RS, ux);
-          st2(r0 + (R_UY) * RS, -uy);
+          rst<NT>(r0 + (R_UX) * RS, ux);
+          rst<NT>(r0 + (R_UY) * RS, -uy);
         }
         // collision of the staged row q - 1
         const float *st = g1;
@@ -350,12 +357,12 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         if (P.var_eta) e = 1.0f / (P.e_c0 + P.e_c1 * rho);
         const F2 fm2 = (P.G * P.G) * (sx * sx + sy * sy);
         collide(P, fd, rho, ux, uy, Fx, Fy, fm2, ev(qf * qs), ev(qf * qd), ev(qf * qxy), e);
-        st2(r1 + (R_F1 + 0) * RS, fd[1]);
-        st2(r1 + (R_F1 + 1) * RS, fd[3]);
-        st2(r1 + (R_F1 + 2) * RS, fd[5]);
-        st2(r1 + (R_F1 + 3) * RS, fd[6]);
-        st2(r1 + (R_F1 + 4) * RS, fd[7]);
-        st2(r1 + (R_F1 + 5) * RS, fd[8]);
+        rst<NT>(r1 + (R_F1 + 0) * RS, fd[1]);
+        rst<NT>(r1 + (R_F1 + 1) * RS, fd[3]);
+        rst<NT>(r1 + (R_F1 + 2) * RS, fd[5]);
+        rst<NT>(r1 + (R_F1 + 3) * RS, fd[6]);
+        rst<NT>(r1 + (R_F1 + 4) * RS, fd[7]);
+        rst<NT>(r1 + (R_F1 + 5) * RS, fd[8]);
         f0n = fd[0];
         f2n = fd[2];
         f4 = fd[4];
@@ -363,8 +370,8 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         Fyn = Fy;
         irn = inv_rho;
       } else if (!SIMPLE && ENERGY && r == P.ny && P.hbc[3] == WALL) {  // mirror ghost of row ny = row ny - 2
-        st2(r1 + (R_UX) * RS, ld2(r0 + (R_UX) * RS));
-        st2(r1 + (R_UY) * RS, -ld2(r0 + (R_UY) * RS));
+        rst<NT>(r1 + (R_UX) * RS, rld<NT>(r0 + (R_UX) * RS));
+        rst<NT>(r1 + (R_UY) * RS, -rld<NT>(r0 + (R_UY) * RS));
       }
       __syncthreads();
     }
@@ -380,14 +387,14 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi)
         F2 fd[9];
         fd[0] = f0c;
-        fd[1] = tripp(r2 + (R_F1 + 0) * RS).l;
+        fd[1] = rtrip<NT>(r2 + (R_F1 + 0) * RS).l;
         fd[2] = f2cc;
-        fd[3] = tripp(r2 + (R_F1 + 1) * RS).r;
+        fd[3] = rtrip<NT>(r2 + (R_F1 + 1) * RS).r;
         fd[4] = f4;
-        fd[5] = tripp(r0 + (R_F1 + 2) * RS).l;
-        fd[6] = tripp(r0 + (R_F1 + 3) * RS).r;
-        fd[7] = tripp(r1 + (R_F1 + 4) * RS).r;
-        fd[8] = tripp(r1 + (R_F1 + 5) * RS).l;
+        fd[5] = rtrip<NT>(r0 + (R_F1 + 2) * RS).l;
+        fd[6] = rtrip<NT>(r0 + (R_F1 + 3) * RS).r;
+        fd[7] = rtrip<NT>(r1 + (R_F1 + 4) * RS).r;
+        fd[8] = rtrip<NT>(r1 + (R_F1 + 5) * RS).l;
         if (!SIMPLE && rm.wall >= 0) zou_he<F2>(rm.wall, fd, ev(-0.5f * Fxc), ev(-0.5f * Fyc));
         const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const F2 rho_new = P.rho_ref + delta;
@@ -395,7 +402,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
 #pragma unroll
         for (int i = 0; i < 9; ++i) st2(fout + i * plane + k, fd[i]);
         if (!ENERGY) {
-          const F2 T_old = ld2(r2 + (R_T) * RS);
+          const F2 T_old = rld<NT>(r2 + (R_T) * RS);
           st2(Tout + k, T_old);
           t_sum = t_sum + T_old;
         }
@@ -407,33 +414,33 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         acc_s = tk;
       }
       if (ENERGY) {
-        const Trip rmd = tripp(r2 + (R_RHO) * RS), tm = tripp(r2 + (R_T) * RS);
+        const Trip rmd = rtrip<NT>(r2 + (R_RHO) * RS), tm = rtrip<NT>(r2 + (R_T) * RS);
         if (iq >= 4) {
           if (!rm.solid) {
             PairHeun &c = nxt;
-            const Trip ru = tripp(r1 + (R_RHO) * RS), tu = tripp(r1 + (R_T) * RS);
+            const Trip ru = rtrip<NT>(r1 + (R_RHO) * RS), tu = rtrip<NT>(r1 + (R_T) * RS);
             const F2 rho = rmd.c, T0 = tm.c;
-            const Trip xu = tripp(r1 + (R_UX) * RS), xm = tripp(r2 + (R_UX) * RS), xd = tripp(r0 + (R_UX) * RS);
-            const Trip yu = tripp(r1 + (R_UY) * RS), ym = tripp(r2 + (R_UY) * RS), yd = tripp(r0 + (R_UY) * RS);
+            const Trip xu = rtrip<NT>(r1 + (R_UX) * RS), xm = rtrip<NT>(r2 + (R_UX) * RS), xd = rtrip<NT>(r0 + (R_UX) * RS);
+            const Trip yu = rtrip<NT>(r1 + (R_UY) * RS), ym = rtrip<NT>(r2 + (R_UY) * RS), yd = rtrip<NT>(r0 + (R_UY) * RS);
             const F2 ux = xm.c, uy = ym.c;
             pr_parts(P, rho, &c.A, &c.B);
             c.T0 = T0;
             c.inv_rcv = irc * P.cv_inv;
             c.lam = P.lam_v + P.dlam * (rho - P.rho_v);
             // 9-point stencils; the lower row's share was formed when it was the centre
-            c.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l) + ld2(share + 0 * RS));
-            c.gdy = P.dlam * (third * ru.c + twelfth * (ru.r + ru.l) + ld2(share + 1 * RS));
+            c.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l) + rld<NT>(share + 0 * RS));
+            c.gdy = P.dlam * (third * ru.c + twelfth * (ru.r + ru.l) + rld<NT>(share + 1 * RS));
             c.div = third * (xm.r - xm.l) + twelfth * (xu.r - xu.l - xd.l + xd.r) + third * (yu.c - yd.c) +
                     twelfth * (yu.r + yu.l - yd.l - yd.r);
             F2 Ts;
             if (!SIMPLE && rm.outflow) {
-              Ts = ld2(r0 + (R_TS) * RS);  // outflow row: copy of the first interior row
+              Ts = rld<NT>(r0 + (R_TS) * RS);  // outflow row: copy of the first interior row
               c.k1 = F2(0.0f);
             } else {
-              const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l) + ld2(share + 2 * RS);
-              const F2 gty = third * tu.c + twelfth * (tu.r + tu.l) + ld2(share + 3 * RS);
+              const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l) + rld<NT>(share + 2 * RS);
+              const F2 gty = third * tu.c + twelfth * (tu.r + tu.l) + rld<NT>(share + 3 * RS);
               const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l - 4.0f * T0) +
-                             (1.0f / 6.0f) * (tu.r + tu.l - 4.0f * T0) + ld2(share + 4 * RS);
+                             (1.0f / 6.0f) * (tu.r + tu.l - 4.0f * T0) + rld<NT>(share + 4 * RS);
               // (lambda lap T + grad lambda . grad T - T (dp/dT) div u) / (rho c_v) - u . grad T
               const F2 adv = ux * gtx + uy * gty;
               const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
@@ -450,18 +457,18 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
                 }
               }
             }
-            st2(r2 + (R_TS) * RS, Ts);
-            if (!SIMPLE && r == 1 && P.hbc[2] == WALL) st2(r1 + (R_TS) * RS, Ts);  // mirror ghost of row -1
+            rst<NT>(r2 + (R_TS) * RS, Ts);
+            if (!SIMPLE && r == 1 && P.hbc[2] == WALL) rst<NT>(r1 + (R_TS) * RS, Ts);  // mirror ghost of row -1
           } else if (!SIMPLE && r == P.ny && P.hbc[3] == WALL) {
-            st2(r2 + (R_TS) * RS, ld2(r1 + (R_TS) * RS));  // mirror ghost of row ny
+            rst<NT>(r2 + (R_TS) * RS, rld<NT>(r1 + (R_TS) * RS));  // mirror ghost of row ny
           }
         }
         // this row's share of the stencils of the row above (used by the next iteration)
-        st2(share + 0 * RS, ev(twelfth * (rmd.r - rmd.l)));
-        st2(share + 1 * RS, -(third * rmd.c + twelfth * (rmd.l + rmd.r)));
-        st2(share + 2 * RS, ev(twelfth * (tm.r - tm.l)));
-        st2(share + 3 * RS, -(third * tm.c + twelfth * (tm.l + tm.r)));
-        st2(share + 4 * RS, (2.0f / 3.0f) * tm.c + (1.0f / 6.0f) * (tm.l + tm.r));
+        rst<NT>(share + 0 * RS, ev(twelfth * (rmd.r - rmd.l)));
+        rst<NT>(share + 1 * RS, -(third * rmd.c + twelfth * (rmd.l + rmd.r)));
+        rst<NT>(share + 2 * RS, ev(twelfth * (tm.r - tm.l)));
+        rst<NT>(share + 3 * RS, -(third * tm.c + twelfth * (tm.l + tm.r)));
+        rst<NT>(share + 4 * RS, (2.0f / 3.0f) * tm.c + (1.0f / 6.0f) * (tm.l + tm.r));
         // the second Heun stage reads this iteration's T*, and the next first stage overwrites
         // the rho and T ring rows read above
         __syncthreads();
@@ -474,13 +481,13 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       const LineMap rm = row_map(r);
       if (!rm.outflow) {
         const PairHeun &c = cur;
-        const Trip tm = tripp(r0 + (R_TS) * RS), tu = tripp(r2 + (R_TS) * RS), td = tripp(r1 + (R_TS) * RS);
+        const Trip tm = rtrip<NT>(r0 + (R_TS) * RS), tu = rtrip<NT>(r2 + (R_TS) * RS), td = rtrip<NT>(r1 + (R_TS) * RS);
         const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l - td.l + td.r);
         const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
         const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * tm.c) +
                        (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * tm.c);
         // u of row q - 3 is still in its ring slot (overwritten by the next collision stage)
-        const F2 adv = ld2(r0 + (R_UX) * RS) * gtx + ld2(r0 + (R_UY) * RS) * gty;
+        const F2 adv = rld<NT>(r0 + (R_UX) * RS) * gtx + rld<NT>(r0 + (R_UY) * RS) * gty;
         const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
         const F2 comp = T_dpdT(P, c.A, c.B, P.T_ref + tm.c) * c.div;
         const F2 k2 = ev((cond - comp) * c.inv_rcv) - adv;
