@@ -107,15 +107,11 @@ __global__ void __launch_bounds__(kAdjNT) adj_node(const AdjParams P, const doub
     const double Ss = t3 * (ps[1] + ps[2] + ps[3] + ps[4]) + t6 * (ps[5] + ps[6] + ps[7] + ps[8]) - 2.0 * psi_c;
     const double Sd = t3 * (ps[1] + ps[3] - ps[2] - ps[4]);
     const double Sxy = t12 * (ps[5] + ps[7] - ps[6] - ps[8]);
-    const double qs = P.kG2 * psi_c * Ss, qd = P.kG2 * psi_c * Sd, qxy = P.kG2 * psi_c * Sxy;
     const double Fx = -P.G * psi_c * sx, Fy = -P.G * psi_c * sy;
     const double fm2 = P.G2 * (sx * sx + sy * sy);
     const double ux = (jx0 + 0.5 * Fx) / rho, uy = (jy0 + 0.5 * Fy) / rho;
     // closed-form collision, forward values needed by its transpose
-    const double s13 = fl[1] + fl[3], s24 = fl[2] + fl[4], s57 = fl[5] + fl[7], s68 = fl[6] + fl[8];
     const double jx = rho * ux, jy = rho * uy;
-    const double y2 = jy * uy;
-    const double ru2 = jx * ux + y2;
     const double e = P.e, g = 0.25 - 0.5 * e;
     // ---- transpose, from the post-collision populations back ----
     double fb[9];  // fbar*_i(x) = fbar^{n+1}_i(x + c_i)

@@ -360,7 +360,9 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
   P.cv_inv = (real)(1.0 / c.cv);
   P.sqrt_Tc_inv = (real)(1.0 / std::sqrt(Tc));
   for (int i = 0; i < 9; ++i) P.s[i] = (real)c.s[i];
-  P.var_eta = (c.eta_l > 0 && c.eta_v > 0) ? 1 : 0;
+  // eta(rho) enters as a per-node rate only where the two phases' viscosities differ; equal
+  // ones give the constant s_eta = 1 / (3 eta + 1/2) (below)
+  P.var_eta = (c.eta_l > 0 && c.eta_v > 0 && c.eta_l != c.eta_v) ? 1 : 0;
   P.eta_l = (real)c.eta_l;
   P.eta_v = (real)c.eta_v;
   P.rho_l = (real)c.rho_l;
@@ -400,7 +402,8 @@ void fill_params(ppl_sim *h, Params<real> &P, const real *const *rw, const real 
     const double e1 = P.var_eta ? 12.0 * (c.eta_l - c.eta_v) / (c.rho_l - c.rho_v) : 0.0;
     P.e_c1 = (real)e1;
     P.e_c0 = (real)(12.0 * c.eta_v + 2.0 - e1 * c.rho_v);
-    P.e_const = (real)(0.25 * s[7]);
+    P.e_const = (c.eta_l > 0 && c.eta_v > 0 && c.eta_l == c.eta_v) ? (real)(0.25 / (3.0 * c.eta_l + 0.5))
+                                                                    : (real)(0.25 * s[7]);
   }
   P.mod_psi = c.contact_model == PPL_CONTACT_MOD_PSI ? 1 : 0;
   P.Gw_over_G = (real)(c.G_w / c.G);
