@@ -30,7 +30,7 @@
 // q-3), the first Heun stage T* (rows q-2 .. q-4) and the staged rows (q-1 .. q+1). The
 // stencils of the first Heun stage reach rho and T one row further down (q-3); that row's
 // share of each stencil is formed one iteration earlier, when the row is the stencil's
-// centre, and kept in thread-private shared memory. With every ring of period three, the
+// centre, and kept in registers (each thread's own columns). With every ring of period three, the
 // slots are addressed through three per-thread pointers that rotate once per iteration,
 // so every ring access is a fixed offset from one of them.
 //
@@ -121,17 +121,22 @@ __host__ __device__ constexpr int pair_ring_stride() {
 }
 constexpr int kPairSlots = 3;      // staged rows and ring rows per quantity
 constexpr int kPairRingRows = 12;  // ring rows per slot: psi, rho, T, ux, uy, f*_{1,3,5,6,7,8}, T*
-constexpr int kPairShareRows = 5;  // a row's shares of the stencils of the row above (thread-private)
 template <int NT>
 constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is aligned up to 128 bytes
-  return (size_t)(kPairSlots * 10 * (2 * NT) + (kPairSlots * kPairRingRows + kPairShareRows) * pair_ring_stride<NT>()) *
-             sizeof(float) +
+  return (size_t)(kPairSlots * 10 * (2 * NT) + kPairSlots * kPairRingRows * pair_ring_stride<NT>()) * sizeof(float) +
          128;
 }
 
-// first Heun stage of a row, handed from S3 to S4 of the next iteration
+// The right-hand side of the energy equation (Eq. energy-equation) at a node, with the
+// pressure split p = T A(rho) - alpha(T) B(rho) (alpha = (1 + k (1 - sqrt(T / Tc)))^2):
+//   L(T) = (lambda lap T + grad lambda . grad T - T (dp/dT)_rho div u) / (rho c_v) - u . grad T
+// and T (dp/dT)_rho = T (A - k^2 B / Tc) + k (1 + k) B sqrt(T / Tc). Both Heun stages of a row
+// evaluate L with the same rho and u, so the first stage folds them into five coefficients
+//   L(T) = lr lap T + vx dT/dx + vy dT/dy + T nA + sqrt(T) nB
+// (lr = lambda / (rho c_v), v = grad lambda / (rho c_v) - u, nA and nB the compression term
+// times -div u / (rho c_v)), which it hands to the second stage with h = T^n + L(T^n) / 2.
 struct PairHeun {
-  F2 k1, lam, gdx, gdy, div, inv_rcv, A, B, T0;
+  F2 h, lr, vx, vy, nA, nB;
 };
 
 // One tile of the step: strip bx (2 NT - 8 interior columns) and row block by (H rows), CTA
@@ -155,13 +160,11 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   // ring rows of a slot s at rings + (s * kPairRingRows + k) * RS + 2 for quantity k (columns
   // -2, -1, SW, SW + 1 are the pads); the slots are addressed by role through three rotating
   // per-thread pointers (below), so every ring access is a fixed offset from one of them
-  // shares of the stencils of the first Heun stage that the row below the centre contributes
-  // (grad rho x, y; grad T x, y; Laplacian of T), formed when that row was the centre; each
-  // thread reads back only its own columns
-  float *share = rings + kPairSlots * kPairRingRows * RS + 1 + threadIdx.x;
   enum { R_PSI = 0, R_RHO = 1, R_T = 2, R_UX = 3, R_UY = 4, R_F1 = 5, R_TS = 11 };
   const float third = 1.0f / 3.0f, twelfth = 1.0f / 12.0f;
   const float big = 3.0e38f;
+  // T (dp/dT)_rho = T (A + kA B) + sqrt(T) (kB B)
+  const float kA = -P.k * P.k / P.Tc, kB = P.k * (1.0f + P.k) * P.sqrt_Tc_inv;
 
   const int t = threadIdx.x;
   const int c2 = 2 * t;  // strip column of lane 0
@@ -243,12 +246,15 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   int k0 = 0, k1 = 2, k2 = 1;  // slot numbers of the roles (TMA destination, mbarrier)
   unsigned ph = 0;              // mbarrier parity per slot (bit k)
   // values carried between stages and iterations, by row
-  F2 jn_x(0.0f), jn_y(0.0f), jc_x(0.0f), jc_y(0.0f);  // S1 (row q) -> S2 (row q - 1, next iteration)
   F2 f0n(0.0f), f0c(0.0f);                             // S2 (row q - 1) -> S3 (row q - 2, next)
   F2 f2n(0.0f), f2c(0.0f), f2cc(0.0f);                 // f_2 of rows q - 1, q - 2, q - 3
   F2 Fxn(0.0f), Fyn(0.0f), Fxc(0.0f), Fyc(0.0f), irn(0.0f), irc(0.0f);  // F and 1/rho, S2 -> S3
   F2 f4(0.0f);  // post-collision f_4 of row q - 1, streamed down into row q - 2 in the same iteration
   PairHeun nxt{}, cur{};  // S3 (row q - 2) -> S4 (row q - 3, next iteration)
+  // shares of the stencils of the first Heun stage that the row below the centre contributes
+  // (grad rho x, y; grad T x, y; Laplacian of T), formed when that row was the centre (S3 reads
+  // them before it forms the next row's, so they need no second set of registers)
+  F2 sh0(0.0f), sh1(0.0f), sh2(0.0f), sh3(0.0f), sh4(0.0f);
 
   for (int iq = 0; iq < n_it; ++iq) {
     const int q = ya - 3 + iq;
@@ -279,9 +285,6 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       rst<NT>(r0 + (R_PSI) * RS, psi);
       rst<NT>(r0 + (R_RHO) * RS, rho);
       rst<NT>(r0 + (R_T) * RS, Tt);
-      const F2 d57 = f[5] - f[7], d68 = f[6] - f[8];
-      jn_x = (f[1] - f[3]) + (d57 - d68);
-      jn_y = (f[2] - f[4]) + (d57 + d68);
     }
     if (use_tma) {
       // a row that did not land stops the CTA (uniformly): the copies already issued are
@@ -340,8 +343,14 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         const F2 fmx = gps * sx, fmy = gps * sy;
         const F2 Fx = fmx + P.gx * (rho - rho_bar), Fy = fmy + P.gy * (rho - rho_bar);
         const F2 inv_rho = 1.0f / rho;
-        const F2 ux = (jc_x + 0.5f * Fx) * inv_rho;
-        const F2 uy = (jc_y + 0.5f * Fy) * inv_rho;
+        // the staged row q - 1 (collided below), and its momentum j = sum f c
+        const float *st = g1;
+        F2 fd[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fd[i] = ld2(st + i * SW);
+        const F2 g57 = fd[5] - fd[7], g68 = fd[6] - fd[8];
+        const F2 ux = ((fd[1] - fd[3]) + (g57 - g68) + 0.5f * Fx) * inv_rho;
+        const F2 uy = ((fd[2] - fd[4]) + (g57 + g68) + 0.5f * Fy) * inv_rho;
         rst<NT>(r1 + (R_UX) * RS, ux);
         rst<NT>(r1 + (R_UY) * RS, uy);
         if (!SIMPLE && ENERGY && r == 1 && P.hbc[2] == WALL) {  // mirror ghost of row -1 (slot of row q - 3)
@@ -349,10 +358,6 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           rst<NT>(r0 + (R_UY) * RS, -uy);
         }
         // collision of the staged row q - 1
-        const float *st = g1;
-        F2 fd[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fd[i] = ld2(st + i * SW);
         F2 e(P.e_const);  // s_eta / 4
         if (P.var_eta) e = 1.0f / (P.e_c0 + P.e_c1 * rho);
         const F2 fm2 = (P.G * P.G) * (sx * sx + sy * sy);
@@ -422,38 +427,38 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
             const F2 rho = rmd.c, T0 = tm.c;
             const Trip xu = rtrip<NT>(r1 + (R_UX) * RS), xm = rtrip<NT>(r2 + (R_UX) * RS), xd = rtrip<NT>(r0 + (R_UX) * RS);
             const Trip yu = rtrip<NT>(r1 + (R_UY) * RS), ym = rtrip<NT>(r2 + (R_UY) * RS), yd = rtrip<NT>(r0 + (R_UY) * RS);
-            const F2 ux = xm.c, uy = ym.c;
-            pr_parts(P, rho, &c.A, &c.B);
-            c.T0 = T0;
-            c.inv_rcv = irc * P.cv_inv;
-            c.lam = P.lam_v + P.dlam * (rho - P.rho_v);
+            F2 A, B;
+            pr_parts(P, rho, &A, &B);
+            const F2 ir = irc * P.cv_inv;  // 1 / (rho c_v)
+            const F2 di = P.dlam * ir;     // d lambda / d rho / (rho c_v)
+            c.lr = (P.lam_v + P.dlam * (rho - P.rho_v)) * ir;
             // 9-point stencils; the lower row's share was formed when it was the centre
-            c.gdx = P.dlam * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l) + rld<NT>(share + 0 * RS));
-            c.gdy = P.dlam * (third * ru.c + twelfth * (ru.r + ru.l) + rld<NT>(share + 1 * RS));
-            c.div = third * (xm.r - xm.l) + twelfth * (xu.r - xu.l - xd.l + xd.r) + third * (yu.c - yd.c) +
-                    twelfth * (yu.r + yu.l - yd.l - yd.r);
+            c.vx = di * (third * (rmd.r - rmd.l) + twelfth * (ru.r - ru.l) + sh0) - xm.c;
+            c.vy = di * (third * ru.c + twelfth * (ru.r + ru.l) + sh1) - ym.c;
+            const F2 ndiv = (-third) * (xm.r - xm.l) + (-twelfth) * (xu.r - xu.l - xd.l + xd.r) +
+                            (-third) * (yu.c - yd.c) + (-twelfth) * (yu.r + yu.l - yd.l - yd.r);
+            const F2 s = ndiv * ir;  // -div u / (rho c_v)
+            c.nA = s * (A + kA * B);
+            c.nB = s * ev(kB * B);
             F2 Ts;
             if (!SIMPLE && rm.outflow) {
               Ts = rld<NT>(r0 + (R_TS) * RS);  // outflow row: copy of the first interior row
-              c.k1 = F2(0.0f);
+              c.h = T0;
             } else {
-              const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l) + rld<NT>(share + 2 * RS);
-              const F2 gty = third * tu.c + twelfth * (tu.r + tu.l) + rld<NT>(share + 3 * RS);
+              const F2 gtx = third * (tm.r - tm.l) + twelfth * (tu.r - tu.l) + sh2;
+              const F2 gty = third * tu.c + twelfth * (tu.r + tu.l) + sh3;
               const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l - 4.0f * T0) +
-                             (1.0f / 6.0f) * (tu.r + tu.l - 4.0f * T0) + rld<NT>(share + 4 * RS);
-              // (lambda lap T + grad lambda . grad T - T (dp/dT) div u) / (rho c_v) - u . grad T
-              const F2 adv = ux * gtx + uy * gty;
-              const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
-              const F2 comp = T_dpdT(P, c.A, c.B, P.T_ref + T0) * c.div;
-              const F2 k1 = ev((cond - comp) * c.inv_rcv) - adv;
-              c.k1 = k1;
+                             (1.0f / 6.0f) * (tu.r + tu.l - 4.0f * T0) + sh4;
+              const F2 Ta = P.T_ref + T0;
+              const F2 k1 = c.lr * lap + c.vx * gtx + c.vy * gty + Ta * c.nA + sqrt(Ta) * c.nB;
               Ts = T0 + k1;
+              c.h = T0 + 0.5f * k1;
               if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes of a boundary line
                 float tw0, tw1;
                 const bool d0 = t_fixed(P, col0, rm.src, &tw0), d1 = t_fixed(P, col1, rm.src, &tw1);
                 if (d0 || d1) {
                   Ts = F2(d0 ? tw0 - P.T_ref : Ts.lo(), d1 ? tw1 - P.T_ref : Ts.hi());
-                  c.k1 = F2(d0 ? 0.0f : k1.lo(), d1 ? 0.0f : k1.hi());
+                  c.h = F2(d0 ? T0.lo() : c.h.lo(), d1 ? T0.hi() : c.h.hi());
                 }
               }
             }
@@ -464,11 +469,11 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           }
         }
         // this row's share of the stencils of the row above (used by the next iteration)
-        rst<NT>(share + 0 * RS, ev(twelfth * (rmd.r - rmd.l)));
-        rst<NT>(share + 1 * RS, -(third * rmd.c + twelfth * (rmd.l + rmd.r)));
-        rst<NT>(share + 2 * RS, ev(twelfth * (tm.r - tm.l)));
-        rst<NT>(share + 3 * RS, -(third * tm.c + twelfth * (tm.l + tm.r)));
-        rst<NT>(share + 4 * RS, (2.0f / 3.0f) * tm.c + (1.0f / 6.0f) * (tm.l + tm.r));
+        sh0 = twelfth * (rmd.r - rmd.l);
+        sh1 = -(third * rmd.c + twelfth * (rmd.l + rmd.r));
+        sh2 = twelfth * (tm.r - tm.l);
+        sh3 = -(third * tm.c + twelfth * (tm.l + tm.r));
+        sh4 = (2.0f / 3.0f) * tm.c + (1.0f / 6.0f) * (tm.l + tm.r);
         // the second Heun stage reads this iteration's T*, and the next first stage overwrites
         // the rho and T ring rows read above
         __syncthreads();
@@ -486,16 +491,13 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         const F2 gty = third * (tu.c - td.c) + twelfth * (tu.r + tu.l - td.l - td.r);
         const F2 lap = (2.0f / 3.0f) * (tm.r + tu.c + tm.l + td.c - 4.0f * tm.c) +
                        (1.0f / 6.0f) * (tu.r + tu.l + td.l + td.r - 4.0f * tm.c);
-        // u of row q - 3 is still in its ring slot (overwritten by the next collision stage)
-        const F2 adv = rld<NT>(r0 + (R_UX) * RS) * gtx + rld<NT>(r0 + (R_UY) * RS) * gty;
-        const F2 cond = c.lam * lap + c.gdx * gtx + c.gdy * gty;
-        const F2 comp = T_dpdT(P, c.A, c.B, P.T_ref + tm.c) * c.div;
-        const F2 k2 = ev((cond - comp) * c.inv_rcv) - adv;
-        F2 T_new = c.T0 + 0.5f * (c.k1 + k2);
+        const F2 Ta = P.T_ref + tm.c;
+        const F2 k2 = c.lr * lap + c.vx * gtx + c.vy * gty + Ta * c.nA + sqrt(Ta) * c.nB;
+        F2 T_new = c.h + 0.5f * k2;
         if ((!SIMPLE && (rm.src == 0 || rm.src == P.ny - 1)) || col_fix) {  // Dirichlet nodes keep their value
           float tw;
           const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
-          T_new = F2(d0 ? c.T0.lo() : T_new.lo(), d1 ? c.T0.hi() : T_new.hi());
+          T_new = F2(d0 ? c.h.lo() : T_new.lo(), d1 ? c.h.hi() : T_new.hi());  // h = T^n there
         }
         st2(Tout + (long long)r * P.nx, T_new);
         t_sum = t_sum + T_new;
@@ -503,8 +505,6 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
     }
     // hand over to the next iteration: carried values by row, slot roles rotated
     if (use_tma) ph ^= 1u << k0;
-    jc_x = jn_x;
-    jc_y = jn_y;
     f0c = f0n;
     f2cc = f2c;
     f2c = f2n;
