@@ -120,10 +120,15 @@ __host__ __device__ constexpr int pair_ring_stride() {
   return 2 * NT + 4;
 }
 constexpr int kPairSlots = 3;      // staged rows and ring rows per quantity
-constexpr int kPairRingRows = 12;  // ring rows per slot: psi, rho, T, ux, uy, f*_{1,3,5,6,7,8}, T*
+constexpr int kPairRingRows = 8;  // ring rows per slot: psi, rho, T, ux, uy, f*_5, f*_6, T*
+// Post-collision populations that stream sideways or down are read sooner than the slot period:
+// f*_7, f*_8 of row q - 1 by the streaming of row q - 2 in the same iteration (one buffer), and
+// f*_1, f*_3 in the next iteration (two buffers, alternating)
+constexpr int kPairBufRows = 6;
 template <int NT>
 constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is aligned up to 128 bytes
-  return (size_t)(kPairSlots * 10 * (2 * NT) + kPairSlots * kPairRingRows * pair_ring_stride<NT>()) * sizeof(float) +
+  return (size_t)(kPairSlots * 10 * (2 * NT) + (kPairSlots * kPairRingRows + kPairBufRows) * pair_ring_stride<NT>()) *
+             sizeof(float) +
          128;
 }
 
@@ -151,16 +156,16 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   constexpr int W = SW - 8;   // interior columns
   static_assert(W % 4 == 0, "strip starts must stay 16-byte aligned for the TMA copies");
   constexpr int RS = pair_ring_stride<NT>();
-  constexpr int NRING = kPairSlots * kPairRingRows;
+  constexpr int NRING = kPairSlots * kPairRingRows + kPairBufRows;
   const unsigned raw_s = (unsigned)__cvta_generic_to_shared(smem_raw);
   float *stg = reinterpret_cast<float *>(smem_raw + ((128u - (raw_s & 127u)) & 127u));  // [3][10][SW]
   float *rings = stg + kPairSlots * 10 * SW;
-  // ring row (quantity k, slot s) at rings + (s * kPairRingRows + k) * RS + 2; columns -2, -1,
-  // SW, SW + 1 are the pads
-  // ring rows of a slot s at rings + (s * kPairRingRows + k) * RS + 2 for quantity k (columns
-  // -2, -1, SW, SW + 1 are the pads); the slots are addressed by role through three rotating
-  // per-thread pointers (below), so every ring access is a fixed offset from one of them
-  enum { R_PSI = 0, R_RHO = 1, R_T = 2, R_UX = 3, R_UY = 4, R_F1 = 5, R_TS = 11 };
+  // ring row of quantity k in slot s at rings + (s * kPairRingRows + k) * RS, laid out as
+  // [pad, even columns, pad, pad, odd columns, pad]; after the three slots the two f*_1, f*_3
+  // buffers (two rows each) and the f*_7, f*_8 buffer. The slots are addressed by role through
+  // three rotating per-thread pointers (below), so every ring access is a fixed offset from one
+  // of them
+  enum { R_PSI = 0, R_RHO = 1, R_T = 2, R_UX = 3, R_UY = 4, R_F5 = 5, R_F6 = 6, R_TS = 7 };
   const float third = 1.0f / 3.0f, twelfth = 1.0f / 12.0f;
   const float big = 3.0e38f;
   // T (dp/dT)_rho = T (A + kA B) + sqrt(T) (kB B)
@@ -242,6 +247,8 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   // Each iteration rotates the roles (0, 1, 2) <- (2, 0, 1).
   float *r0 = rings + 0 * kPairRingRows * RS + 1 + t, *r1 = rings + 2 * kPairRingRows * RS + 1 + t,
         *r2 = rings + 1 * kPairRingRows * RS + 1 + t;
+  // f*_1, f*_3 buffers: written for row q - 1 (f13w), read for row q - 2 (f13r); f*_7, f*_8: f78
+  float *f13w = rings + kPairSlots * kPairRingRows * RS + 1 + t, *f13r = f13w + 2 * RS, *const f78 = f13w + 4 * RS;
   const float *g0 = stg + 0 * 10 * SW + c2, *g1 = stg + 2 * 10 * SW + c2, *g2 = stg + 1 * 10 * SW + c2;
   int k0 = 0, k1 = 2, k2 = 1;  // slot numbers of the roles (TMA destination, mbarrier)
   unsigned ph = 0;              // mbarrier parity per slot (bit k)
@@ -362,12 +369,12 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         if (P.var_eta) e = 1.0f / (P.e_c0 + P.e_c1 * rho);
         const F2 fm2 = (P.G * P.G) * (sx * sx + sy * sy);
         collide(P, fd, rho, ux, uy, Fx, Fy, fm2, ev(qf * qs), ev(qf * qd), ev(qf * qxy), e);
-        rst<NT>(r1 + (R_F1 + 0) * RS, fd[1]);
-        rst<NT>(r1 + (R_F1 + 1) * RS, fd[3]);
-        rst<NT>(r1 + (R_F1 + 2) * RS, fd[5]);
-        rst<NT>(r1 + (R_F1 + 3) * RS, fd[6]);
-        rst<NT>(r1 + (R_F1 + 4) * RS, fd[7]);
-        rst<NT>(r1 + (R_F1 + 5) * RS, fd[8]);
+        rst<NT>(f13w, fd[1]);
+        rst<NT>(f13w + RS, fd[3]);
+        rst<NT>(r1 + (R_F5) * RS, fd[5]);
+        rst<NT>(r1 + (R_F6) * RS, fd[6]);
+        rst<NT>(f78, fd[7]);
+        rst<NT>(f78 + RS, fd[8]);
         f0n = fd[0];
         f2n = fd[2];
         f4 = fd[4];
@@ -392,14 +399,14 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi)
         F2 fd[9];
         fd[0] = f0c;
-        fd[1] = rtrip<NT>(r2 + (R_F1 + 0) * RS).l;
+        fd[1] = rtrip<NT>(f13r).l;
         fd[2] = f2cc;
-        fd[3] = rtrip<NT>(r2 + (R_F1 + 1) * RS).r;
+        fd[3] = rtrip<NT>(f13r + RS).r;
         fd[4] = f4;
-        fd[5] = rtrip<NT>(r0 + (R_F1 + 2) * RS).l;
-        fd[6] = rtrip<NT>(r0 + (R_F1 + 3) * RS).r;
-        fd[7] = rtrip<NT>(r1 + (R_F1 + 4) * RS).r;
-        fd[8] = rtrip<NT>(r1 + (R_F1 + 5) * RS).l;
+        fd[5] = rtrip<NT>(r0 + (R_F5) * RS).l;
+        fd[6] = rtrip<NT>(r0 + (R_F6) * RS).r;
+        fd[7] = rtrip<NT>(f78).r;
+        fd[8] = rtrip<NT>(f78 + RS).l;
         if (!SIMPLE && rm.wall >= 0) zou_he<F2>(rm.wall, fd, ev(-0.5f * Fxc), ev(-0.5f * Fyc));
         const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const F2 rho_new = P.rho_ref + delta;
@@ -525,6 +532,9 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       k2 = k1;
       k1 = k0;
       k0 = kt;
+      float *ft = f13w;
+      f13w = f13r;
+      f13r = ft;
     }
   }
   cp_async_wait<0>();
@@ -540,7 +550,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
 }
 
 template <bool ENERGY, int NT>
-__global__ void __launch_bounds__(NT, 384 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
+__global__ void __launch_bounds__(NT, 448 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long bars[kPairSlots];  // mbarriers of the TMA staging slots
   const int ya = blockIdx.y * H;
