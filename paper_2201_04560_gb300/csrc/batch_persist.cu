@@ -142,8 +142,7 @@ __global__ void __launch_bounds__(NT, 384 / NT) persistent_batch(const PersistMe
     // cross-proxy fences to see; the staging path does not change the results
     io.tmap_f = nullptr;
     io.tmap_T = nullptr;
-    const int ya = by * M.H, yb = min(ya + M.H, P.ny);
-    const bool simple = ya - 3 >= 1 && yb + 2 <= P.ny - 2;
+    const bool simple = pair_tile_simple<NT>(P, M.H, bx, by);
     const bool energy = M.energy_on && M.step0 + (long long)j >= M.iso_steps;
     unsigned *done = &ctl->done[e.mesh];
     const unsigned nblk = (unsigned)(M.gx * M.gy);

@@ -132,6 +132,17 @@ constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is ali
          128;
 }
 
+// Whether tile (bx, by) of H rows takes the specialisation without boundary logic: its rows and
+// their 3-row halo lie inside the domain, and its strip holds no column of a thermally
+// non-periodic x line (Dirichlet temperatures on x = 0 or x = nx - 1).
+template <int NT>
+__device__ __forceinline__ bool pair_tile_simple(const Params<float> &P, int H, int bx, int by) {
+  const int ya = by * H, yb = min(ya + H, P.ny);
+  const int g0 = bx * (2 * NT - 8) - 4, g1 = g0 + 2 * NT - 1;  // first and last strip column
+  const bool xfix = (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (g0 <= 0 || g1 >= P.nx - 1);
+  return ya - 3 >= 1 && yb + 2 <= P.ny - 2 && !xfix;
+}
+
 // The right-hand side of the energy equation (Eq. energy-equation) at a node, with the
 // pressure split p = T A(rho) - alpha(T) B(rho) (alpha = (1 + k (1 - sqrt(T / Tc)))^2):
 //   L(T) = (lambda lap T + grad lambda . grad T - T (dp/dT)_rho div u) / (rho c_v) - u . grad T
@@ -181,7 +192,9 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   if (src0 < 0) src0 += P.nx;
   const int col0 = src0, col1 = src0 + 1;  // in-domain columns of the two lanes
   // a lane on a thermally non-periodic x line (e.g. a Dirichlet ring around a periodic box)
-  const bool col_fix = (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (col0 == 0 || col1 == P.nx - 1);
+  // (never in the SIMPLE specialisation, which such strips do not take)
+  const bool col_fix =
+      !SIMPLE && (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (col0 == 0 || col1 == P.nx - 1);
   const long long plane = P.plane;
   const float rho_bar = (float)io.stats_in[0];
   const bool any_outflow = P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
@@ -395,8 +408,9 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
     if (iq >= 3) {
       const int r = q - 2;
       const LineMap rm = row_map(r);
-      if (iq >= 5 && r < yb && t_in && !rm.outflow) {
-        // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi)
+      if (iq >= 5 && r < yb && !rm.outflow) {
+        // pull f_i(x) = f*_i(x - c_i) from the ring rows r-1 (lo), r (mid), r+1 (hi); the halo
+        // lanes compute alongside and store nothing
         F2 fd[9];
         fd[0] = f0c;
         fd[1] = rtrip<NT>(f13r).l;
@@ -411,19 +425,21 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
         const F2 delta = ((fd[0] + (fd[1] + fd[2]) + (fd[3] + fd[4])) + ((fd[5] + fd[6]) + (fd[7] + fd[8])));
         const F2 rho_new = P.rho_ref + delta;
         const long long k = (long long)r * P.nx;
+        if (t_in) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st2(fout + i * plane + k, fd[i]);
-        if (!ENERGY) {
-          const F2 T_old = rld<NT>(r2 + (R_T) * RS);
-          st2(Tout + k, T_old);
-          t_sum = t_sum + T_old;
+          for (int i = 0; i < 9; ++i) st2(fout + i * plane + k, fd[i]);
+          if (!ENERGY) {
+            const F2 T_old = rld<NT>(r2 + (R_T) * RS);
+            st2(Tout + k, T_old);
+            t_sum = t_sum + T_old;
+          }
+          rho_min = fminf(rho_min, fminf(rho_new.lo(), rho_new.hi()));
+          const float wr = (!SIMPLE && any_outflow) ? (float)line_weight(r, P.ny, P.hbc[2], P.hbc[3]) : 1.0f;
+          const F2 yk = wr * rho_new + acc_n;
+          const F2 tk = acc_s + yk;
+          acc_n = yk - (tk - acc_s);
+          acc_s = tk;
         }
-        rho_min = fminf(rho_min, fminf(rho_new.lo(), rho_new.hi()));
-        const float wr = (!SIMPLE && any_outflow) ? (float)line_weight(r, P.ny, P.hbc[2], P.hbc[3]) : 1.0f;
-        const F2 yk = wr * rho_new + acc_n;
-        const F2 tk = acc_s + yk;
-        acc_n = yk - (tk - acc_s);
-        acc_s = tk;
       }
       if (ENERGY) {
         const Trip rmd = rtrip<NT>(r2 + (R_RHO) * RS), tm = rtrip<NT>(r2 + (R_T) * RS);
@@ -488,7 +504,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
     }
 
     // ---- S4: row q-3 (second Heun stage, store of T) ----
-    if (ENERGY && iq >= 6 && t_in) {
+    if (ENERGY && iq >= 6) {  // the halo lanes compute alongside and store nothing
       const int r = q - 3;
       const LineMap rm = row_map(r);
       if (!rm.outflow) {
@@ -506,8 +522,10 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
           const bool d0 = t_fixed(P, col0, rm.src, &tw), d1 = t_fixed(P, col1, rm.src, &tw);
           T_new = F2(d0 ? c.h.lo() : T_new.lo(), d1 ? c.h.hi() : T_new.hi());  // h = T^n there
         }
-        st2(Tout + (long long)r * P.nx, T_new);
-        t_sum = t_sum + T_new;
+        if (t_in) {
+          st2(Tout + (long long)r * P.nx, T_new);
+          t_sum = t_sum + T_new;
+        }
       }
     }
     // hand over to the next iteration: carried values by row, slot roles rotated
@@ -553,10 +571,8 @@ template <bool ENERGY, int NT>
 __global__ void __launch_bounds__(NT, 448 / NT) row_step_pair(const Params<float> P, const StepIO io, const int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long bars[kPairSlots];  // mbarriers of the TMA staging slots
-  const int ya = blockIdx.y * H;
-  const int yb = min(ya + H, P.ny);
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-  if (ya - 3 >= 1 && yb + 2 <= P.ny - 2)
+  if (pair_tile_simple<NT>(P, H, blockIdx.x, blockIdx.y))
     row_body_pair<ENERGY, NT, true>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
   else
     row_body_pair<ENERGY, NT, false>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
