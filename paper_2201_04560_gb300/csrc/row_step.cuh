@@ -152,7 +152,18 @@ __device__ __forceinline__ void tile_mass_finalize(const Params<PT> &P, const St
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       s[j] = 0.0;
-      for (unsigned b = t; b < nblk; b += NT) s[j] += __ldcg(io.partials + (size_t)b * K + j);
+      // the partials in the order b = t, t + NT, ..., loaded eight at a time so that their
+      // latencies overlap (this CTA runs alone at the end of the step)
+      for (unsigned b0 = t; b0 < nblk; b0 += 8 * NT) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const unsigned b = b0 + u * NT;
+          x[u] = b < nblk ? __ldcg(io.partials + (size_t)b * K + j) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[j] += x[u];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
     }
