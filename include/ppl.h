@@ -431,10 +431,13 @@ int ppl_contact_angle(const double *rho, int32_t nx, int32_t ny, int side, doubl
 
 /* ---- launch shape ---- */
 
-/* Rows per CTA of the fused step kernel (the grid is ceil(nx / (NT - 6)) strips of
- * columns x ceil(ny / rows) row blocks; every CTA recomputes 6 halo rows). rows = 0
- * restores the default: one wave of resident CTAs over the rows.
- * 1 <= rows <= ny otherwise (PPL_E_INVAL). Results do not depend on the shape except
+/* Rows per CTA of the fused step kernel (the grid is strips of columns x ceil(ny / rows)
+ * row blocks; every CTA recomputes 6 halo rows). rows = 0 restores the default: one wave
+ * of resident CTAs over the rows, except for the two-column FP32 step on a grid whose wave
+ * would have blocks of 28 rows or more: there one wave of blocks of ~0.86 ny / wave rows
+ * covers the lower part and blocks of ~0.27 times that height the rest, so that CTAs
+ * freed early take short blocks and the SMs stay full until the step ends.
+ * 1 <= rows <= ny otherwise (PPL_E_INVAL; uniform blocks). Results do not depend on the shape except
  * through the rounding of the domain-mass sum of Eq. (gravitational_force), which is
  * summed per CTA (last-bit differences of rho_bar where gravity is on). Drops the
  * handle's captured graphs; synchronises. */
@@ -452,6 +455,7 @@ int ppl_set_launch(ppl_t *h, int32_t rows_per_cta);
 #define PPL_KERNEL_PAIR 2
 int ppl_select_kernel(ppl_t *h, int kernel);
 int ppl_get_kernel(const ppl_t *h);
+/* Launch shape in use: rows of the (first) row blocks and CTAs per step launch. */
 int ppl_get_launch(const ppl_t *h, int32_t *rows_per_cta, int32_t *ctas);
 /* 1 if the two-column FP32 step stages rows by TMA (tensor maps of the state were encoded at
  * ppl_init: FP32, nx a multiple of 4 and at least one strip wide), 0 if every strip uses

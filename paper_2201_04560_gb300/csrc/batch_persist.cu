@@ -142,7 +142,10 @@ __global__ void __launch_bounds__(NT, 384 / NT) persistent_batch(const PersistMe
     // cross-proxy fences to see; the staging path does not change the results
     io.tmap_f = nullptr;
     io.tmap_T = nullptr;
-    const bool simple = pair_tile_simple<NT>(P, M.H, bx, by);
+    io.blocks_a = 0;
+    io.fill_rows = 0;
+    const int ya = by * M.H, yb = min(ya + M.H, P.ny);
+    const bool simple = pair_tile_simple<NT>(P, ya, yb, bx);
     const bool energy = M.energy_on && M.step0 + (long long)j >= M.iso_steps;
     unsigned *done = &ctl->done[e.mesh];
     const unsigned nblk = (unsigned)(M.gx * M.gy);
@@ -151,14 +154,14 @@ __global__ void __launch_bounds__(NT, 384 / NT) persistent_batch(const PersistMe
     const bool reduce = !M.local || j + 1 == (unsigned)(n_outer * M.sub);
     if (energy) {
       if (simple)
-        row_body_pair<true, NT, true>(P, io, M.H, bx, by, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+        row_body_pair<true, NT, true>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
       else
-        row_body_pair<true, NT, false>(P, io, M.H, bx, by, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+        row_body_pair<true, NT, false>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
     } else {
       if (simple)
-        row_body_pair<false, NT, true>(P, io, M.H, bx, by, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+        row_body_pair<false, NT, true>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
       else
-        row_body_pair<false, NT, false>(P, io, M.H, bx, by, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1,
+        row_body_pair<false, NT, false>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1,
                                         reduce);
     }
     if (M.local && threadIdx.x == 0) {  // this tile's step is complete (all its threads passed a barrier)

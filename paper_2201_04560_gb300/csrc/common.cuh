@@ -67,6 +67,10 @@ struct StepIO {
   // with a box of one row of the FP32 two-column strip, or null (per-thread row copies)
   const void *tmap_f;
   const void *tmap_T;
+  // row blocks of the launch (two-column step): the first blocks_a have the kernel's H rows,
+  // the others fill_rows rows; fill_rows = 0: all have H rows
+  int blocks_a;
+  int fill_rows;
 };
 
 // lattice of Sec. 2

@@ -445,6 +445,8 @@ int launch_step_t(ppl_sim *h, bool energy) {
   io.status = h->status;
   io.tmap_f = h->tmaps ? (const unsigned char *)h->tmaps + h->cur * sizeof(CUtensorMap) : nullptr;
   io.tmap_T = h->tmaps ? (const unsigned char *)h->tmaps + (2 + h->cur) * sizeof(CUtensorMap) : nullptr;
+  io.blocks_a = h->tall_blocks;
+  io.fill_rows = h->fill_rows;
   int H = h->rows_per_cta;
   void *args[] = {(void *)&P, (void *)&io, (void *)&H};
   CK(cudaLaunchKernel(h->var.fn[energy ? 1 : 0], h->grid, dim3(h->var.nt), args, h->var.smem, h->stream));
@@ -596,6 +598,47 @@ int default_rows(const ppl_sim *h) {
   int yblocks = slots / strips;
   if (yblocks < 1) yblocks = 1;
   return (h->ny + yblocks - 1) / yblocks;  // small grids get short blocks: more CTAs in flight
+}
+
+// Default shape of the two-column step on a large grid: one wave of tall row blocks over the
+// first ~86 % of the rows, then short blocks (~0.27 of the tall height) for the rest. The CTAs
+// resident on an SM do not progress at one rate (the older ones are issued first), so in a
+// single wave of equal blocks the SM's occupancy decays towards the end of the step; the short
+// blocks take the freed slots and keep it full, at the price of their extra halo rows
+// (measured on 2048 x 4096: 53.2 against 49.4 G node updates/s for one uniform wave).
+void default_shape(const ppl_sim *h, int *rows, int *fill_rows) {
+  *rows = default_rows(h);
+  *fill_rows = 0;
+  if (h->var.nt != kNTP || h->prec != PPL_FP32DEV) return;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->var.fn[1], h->var.nt, h->var.smem);
+  const int strips = (h->nx + h->var.width - 1) / h->var.width;
+  const int tall = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) / strips;
+  if (tall < 1) return;
+  const int H1 = (int)std::lround(0.86 * h->ny / tall);
+  if (H1 < 24) return;  // short blocks would be mostly halo
+  const int H2 = std::max(4, (int)std::lround(0.27 * H1));
+  if ((long long)tall * H1 >= h->ny) return;
+  *rows = H1;
+  *fill_rows = H2;
+}
+
+// grid of a launch shape; *tall receives the row blocks of `rows` rows
+dim3 shape_grid(const ppl_sim *h, int rows, int fill_rows, int *tall) {
+  const int strips = (h->nx + h->var.width - 1) / h->var.width;
+  if (fill_rows <= 0) {
+    *tall = (h->ny + rows - 1) / rows;
+    return dim3(strips, *tall);
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->var.fn[1], h->var.nt, h->var.smem);
+  *tall = std::max(1, std::min((sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) / strips, (h->ny - 1) / rows));
+  const int rest = h->ny - *tall * rows;
+  return dim3(strips, *tall + (rest + fill_rows - 1) / fill_rows);
 }
 
 int check_status(ppl_sim *h) {
@@ -759,8 +802,8 @@ int ppl_init(const ppl_config *cfg, const double *rho0, const double *ux0, const
     if (cudaFuncSetAttribute(h->var.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->var.smem) !=
         cudaSuccess)
       return fail(PPL_E_CUDA);
-  h->rows_per_cta = default_rows(h);
-  h->grid = dim3((h->nx + h->var.width - 1) / h->var.width, (h->ny + h->rows_per_cta - 1) / h->rows_per_cta);
+  default_shape(h, &h->rows_per_cta, &h->fill_rows);
+  h->grid = shape_grid(h, h->rows_per_cta, h->fill_rows, &h->tall_blocks);
   h->stats_blocks = 608;
   const size_t nctas = (size_t)h->grid.x * h->grid.y;
   const size_t step_part = nctas * (is_tangent(h->prec) ? 2 : 1);
@@ -1184,6 +1227,8 @@ int ppl_step_noalloc(const ppl_config *cfg, const void *f_in, const void *T_in, 
   io.status = status;
   io.tmap_f = nullptr;  // caller-owned buffers: per-thread row copies
   io.tmap_T = nullptr;
+  io.blocks_a = 0;
+  io.fill_rows = 0;
   const int e = cfg->energy_on ? 1 : 0;
   if (cfg->precision == PPL_FP64) {
     Params<double> P;

@@ -136,8 +136,7 @@ constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is ali
 // their 3-row halo lie inside the domain, and its strip holds no column of a thermally
 // non-periodic x line (Dirichlet temperatures on x = 0 or x = nx - 1).
 template <int NT>
-__device__ __forceinline__ bool pair_tile_simple(const Params<float> &P, int H, int bx, int by) {
-  const int ya = by * H, yb = min(ya + H, P.ny);
+__device__ __forceinline__ bool pair_tile_simple(const Params<float> &P, int ya, int yb, int bx) {
   const int g0 = bx * (2 * NT - 8) - 4, g1 = g0 + 2 * NT - 1;  // first and last strip column
   const bool xfix = (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (g0 <= 0 || g1 >= P.nx - 1);
   return ya - 3 >= 1 && yb + 2 <= P.ny - 2 && !xfix;
@@ -155,11 +154,11 @@ struct PairHeun {
   F2 h, lr, vx, vy, nA, nB;
 };
 
-// One tile of the step: strip bx (2 NT - 8 interior columns) and row block by (H rows), CTA
-// bid of nblk for the mass reduction; `done` as in tile_mass_finalize.
+// One tile of the step: strip bx (2 NT - 8 interior columns) and rows [ya, yb), CTA bid of
+// nblk for the mass reduction; `done` as in tile_mass_finalize.
 // reduce = false skips the mass reduction (a step whose domain mean nobody reads).
 template <bool ENERGY, int NT, bool SIMPLE>
-__device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int H, int bx, int by,
+__device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int ya, const int yb, int bx,
                                               unsigned bid, unsigned nblk, unsigned char *smem_raw,
                                               unsigned long long *bars, unsigned *done = nullptr,
                                               unsigned done_value = 0, bool reduce = true) {
@@ -185,8 +184,6 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   const int t = threadIdx.x;
   const int c2 = 2 * t;  // strip column of lane 0
   const int x0 = bx * W;
-  const int ya = by * H;
-  const int yb = min(ya + H, P.ny);
   const int gx0 = x0 - 4 + c2;  // even
   int src0 = gx0 % P.nx;
   if (src0 < 0) src0 += P.nx;
@@ -572,10 +569,15 @@ __global__ void __launch_bounds__(NT, 448 / NT) row_step_pair(const Params<float
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long bars[kPairSlots];  // mbarriers of the TMA staging slots
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-  if (pair_tile_simple<NT>(P, H, blockIdx.x, blockIdx.y))
-    row_body_pair<ENERGY, NT, true>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
+  // rows of this block: the first io.blocks_a row blocks have H rows, the rest io.fill_rows
+  const int by = blockIdx.y;
+  const bool tall = io.fill_rows <= 0 || by < io.blocks_a;
+  const int ya = tall ? by * H : io.blocks_a * H + (by - io.blocks_a) * io.fill_rows;
+  const int yb = min(ya + (tall ? H : io.fill_rows), P.ny);
+  if (pair_tile_simple<NT>(P, ya, yb, blockIdx.x))
+    row_body_pair<ENERGY, NT, true>(P, io, ya, yb, blockIdx.x, bid, nblk, smem_raw, bars);
   else
-    row_body_pair<ENERGY, NT, false>(P, io, H, blockIdx.x, blockIdx.y, bid, nblk, smem_raw, bars);
+    row_body_pair<ENERGY, NT, false>(P, io, ya, yb, blockIdx.x, bid, nblk, smem_raw, bars);
 }
 
 }  // namespace ppl_dev

@@ -45,6 +45,10 @@ struct ppl_sim {
   StepVariant var;
   dim3 grid;
   int rows_per_cta = 0;
+  // two-height shape of the two-column step: grid.y = tall_blocks row blocks of rows_per_cta
+  // rows, then row blocks of fill_rows rows up to ny (fill_rows = 0: all rows_per_cta)
+  int tall_blocks = 0;
+  int fill_rows = 0;
   int stats_blocks = 0;
   Params<double> pd;
   Params<float> pf;
@@ -81,6 +85,13 @@ bool energy_at(const ppl_sim *h, int64_t step);
 int check_status(ppl_sim *h);
 // default rows per CTA: one wave of resident CTAs over the rows
 int default_rows(const ppl_sim *h);
+// the default launch shape: rows per CTA and, for the two-column step of a large grid, the
+// height of the short row blocks that follow one wave of tall ones (0: uniform)
+void default_shape(const ppl_sim *h, int *rows, int *fill_rows);
+// applies a launch shape (fill_rows = 0: uniform row blocks of `rows` rows)
+int apply_shape(ppl_sim *h, int rows, int fill_rows);
+// grid of a launch shape; *tall receives the number of row blocks of `rows` rows
+dim3 shape_grid(const ppl_sim *h, int rows, int fill_rows, int *tall);
 
 template <typename real>
 const Params<real> &params_of(const ppl_sim *h);

@@ -254,7 +254,8 @@ int batch_capture(ppl_batch *b, const std::vector<int> &pat, cudaGraphExec_t *ou
 bool persistent_applicable(const ppl_batch *b) {
   if (b->sims.size() > (size_t)kPersistMaxMeshes) return false;
   for (auto h : b->sims)
-    if (h->prec != PPL_FP32DEV || h->var.fn[0] != step_variant_fp32_pair().fn[0]) return false;
+    if (h->prec != PPL_FP32DEV || h->var.fn[0] != step_variant_fp32_pair().fn[0] || h->fill_rows > 0)
+      return false;  // (the persistent items address uniform row blocks)
   return true;
 }
 
@@ -545,9 +546,19 @@ void ppl_batch_destroy(ppl_batch_t *b) {
 // ---------------------------------------------------------------------------------
 namespace {
 
-int apply_rows(ppl_sim *h, int H) {
-  const int strips = (h->nx + h->var.width - 1) / h->var.width;
-  const dim3 grid(strips, (h->ny + H - 1) / H);
+int apply_rows(ppl_sim *h, int H) { return apply_shape(h, H, 0); }
+
+int apply_default_shape(ppl_sim *h) {
+  int H, F;
+  default_shape(h, &H, &F);
+  return apply_shape(h, H, F);
+}
+
+}  // namespace
+
+int ppl_host::apply_shape(ppl_sim *h, int H, int fill_rows) {
+  int tall = 0;
+  const dim3 grid = shape_grid(h, H, fill_rows, &tall);
   const size_t nctas = (size_t)grid.x * grid.y;
   CK(cudaStreamSynchronize(h->stream));
   const size_t need = nctas * (is_tangent(h->prec) ? 2 : 1);
@@ -564,18 +575,18 @@ int apply_rows(ppl_sim *h, int H) {
       h->graph[e] = nullptr;
     }
   h->rows_per_cta = H;
+  h->fill_rows = fill_rows > 0 ? fill_rows : 0;
+  h->tall_blocks = tall;
   h->grid = grid;
   h->shape_gen += 1;
   return PPL_OK;
 }
 
-}  // namespace
-
 extern "C" {
 
 int ppl_set_launch(ppl_t *h, int32_t rows_per_cta) {
   if (!h || rows_per_cta < 0 || rows_per_cta > h->ny) return PPL_E_INVAL;
-  return apply_rows(h, rows_per_cta == 0 ? default_rows(h) : rows_per_cta);
+  return rows_per_cta == 0 ? apply_default_shape(h) : apply_rows(h, rows_per_cta);
 }
 
 int ppl_select_kernel(ppl_t *h, int kernel) {
@@ -586,7 +597,7 @@ int ppl_select_kernel(ppl_t *h, int kernel) {
     CK(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
   CK(cudaStreamSynchronize(h->stream));
   h->var = v;
-  return apply_rows(h, default_rows(h));
+  return apply_default_shape(h);
 }
 
 int ppl_get_kernel(const ppl_t *h) {
@@ -658,7 +669,7 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
   // candidates: each applicable kernel (FP32: two-column and one-column) x rows per CTA
   std::vector<int> kernels = {PPL_KERNEL_COLUMN};
   if (pair_applicable(h->cfg)) kernels.insert(kernels.begin(), PPL_KERNEL_PAIR);
-  int best = 0, best_kernel = kernels[0];
+  int best = 0, best_fill = 0, best_kernel = kernels[0];
   float best_t = -1.0f;
   for (size_t kk = 0; kk < kernels.size() && rc == PPL_OK; ++kk) {
     const StepVariant v = pick_variant(h->cfg, kernels[kk]);
@@ -666,11 +677,14 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
       rc = cuda_err(cudaFuncSetAttribute(v.fn[e], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     if (rc != PPL_OK) break;
     h->var = v;
-    std::vector<int> cand = {default_rows(h)};
+    // the default shape (two heights where it applies) and uniform row blocks
+    int dH = 0, dF = 0;
+    default_shape(h, &dH, &dF);
+    std::vector<std::pair<int, int>> cand = {{dH, dF}};
     for (int H : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-      if (H <= h->ny && std::find(cand.begin(), cand.end(), H) == cand.end()) cand.push_back(H);
+      if (H <= h->ny && std::find(cand.begin(), cand.end(), std::make_pair(H, 0)) == cand.end()) cand.push_back({H, 0});
     for (size_t i = 0; i < cand.size() && rc == PPL_OK; ++i) {
-      rc = apply_rows(h, cand[i]);
+      rc = apply_shape(h, cand[i].first, cand[i].second);
       if (rc == PPL_OK) rc = ppl_step_async(h, 2);  // warm-up (and graph capture below)
       if (rc == PPL_OK && steps >= kGraphSteps) rc = ppl_step_async(h, kGraphSteps);
       if (rc == PPL_OK) rc = restore();
@@ -683,13 +697,14 @@ int ppl_autotune(ppl_t *h, int32_t steps, int32_t *best_rows, double *best_ms) {
       if (rc == PPL_OK) rc = restore();
       if (rc == PPL_OK && (best_t < 0.0f || ms < best_t)) {
         best_t = ms;
-        best = cand[i];
+        best = cand[i].first;
+        best_fill = cand[i].second;
         best_kernel = kernels[kk];
       }
     }
   }
   if (rc == PPL_OK) h->var = pick_variant(h->cfg, best_kernel);
-  if (rc == PPL_OK) rc = apply_rows(h, best);
+  if (rc == PPL_OK) rc = apply_shape(h, best, best_fill);
   if (rc == PPL_OK) rc = cuda_err(cudaStreamSynchronize(h->stream));
   cudaFree(sf);
   cudaFree(sT);

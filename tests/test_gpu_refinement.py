@@ -141,6 +141,33 @@ def test_launch_shape_does_not_change_results(ppl, th, precision, rtol):
         s.close()
 
 
+def test_two_height_launch_shape(ppl, th):
+    # a grid large enough for the default two-column shape to follow one wave of tall row
+    # blocks with short ones (pool boiling, gravity off so that the mass sum does not enter,
+    # 2048 x 1800): results agree with one uniform wave to contraction-level rounding
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    c, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=2048, ny=1800, g=0.0, precision="fp32")
+    s = ppl.Simulation(c, *ic)
+    assert s.kernel == "pair"
+    rows, ctas = s.launch()
+    strips = -(-2048 // 120)
+    assert ctas > strips * -(-1800 // rows)  # short row blocks follow the tall ones
+    s.step(30)
+    got = s.fields()
+    assert s.norms()["flags"] == 0
+    s.set_launch(rows)  # uniform blocks of the tall height
+    assert s.launch() == (rows, strips * -(-1800 // rows))
+    s.close()
+    ref = ppl.Simulation(c, *ic)
+    ref.set_launch(rows)
+    ref.step(30)
+    want = ref.fields()
+    ref.close()
+    for k in ("rho", "T"):
+        np.testing.assert_allclose(got[k], want[k], rtol=1e-5, atol=1e-7)
+
+
 def test_autotune_restores_state(ppl, th):
     c, ic = pool(th, 300, 160)
     c.update(gy=-3e-5)
