@@ -117,6 +117,14 @@ constexpr size_t row_step_smem_bytes() {
 // The tile of a step is CTA `bid` of `nblk` (blockIdx / gridDim for a step launch); `done`, if
 // given, is set to `done_value` (release) by the last tile once rho_bar is published (the
 // persistent batch's step-completion flag).
+// Rows [ya, yb) of row block `by` of a launch: the first io.blocks_a blocks have H rows, the
+// others io.fill_rows rows (io.fill_rows = 0: every block has H rows).
+__device__ __forceinline__ void block_rows(const StepIO &io, int H, int by, int ny, int *ya, int *yb) {
+  const bool tall = io.fill_rows <= 0 || by < io.blocks_a;
+  *ya = tall ? by * H : io.blocks_a * H + (by - io.blocks_a) * io.fill_rows;
+  *yb = min(*ya + (tall ? H : io.fill_rows), ny);
+}
+
 template <int NT, bool TANGENT, typename PT>
 __device__ __forceinline__ void tile_mass_finalize(const Params<PT> &P, const StepIO &io, double acc, double dacc,
                                                    unsigned bid, unsigned nblk, unsigned *done = nullptr,
@@ -222,8 +230,8 @@ __device__ __forceinline__ void row_body(const Params<real> &P, const StepIO &io
 
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * W;
-  const int ya = blockIdx.y * H;
-  const int yb = min(ya + H, P.ny);
+  int ya, yb;
+  block_rows(io, H, blockIdx.y, P.ny, &ya, &yb);
   const int gx = x0 - 3 + t;
   const LineMap cm = map_line(gx, P.nx, P.hbc[0], P.hbc[1], 0);
   const bool col_bnd = cm.src == 0 || cm.src == P.nx - 1;  // node may sit on an x boundary line
@@ -576,8 +584,8 @@ template <typename real, bool ENERGY, int NT, int PF>
 __global__ void __launch_bounds__(NT, sizeof(real) == 4 ? 5 : 1) row_step(const Params<real> P, const StepIO io,
                                                                        const int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ya = blockIdx.y * H;
-  const int yb = min(ya + H, P.ny);
+  int ya, yb;
+  block_rows(io, H, blockIdx.y, P.ny, &ya, &yb);
   if (ya - 3 >= 1 && yb + 2 <= P.ny - 2)
     row_body<real, ENERGY, NT, PF, true>(P, io, H, smem_raw);
   else

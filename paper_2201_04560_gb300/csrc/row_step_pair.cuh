@@ -569,11 +569,8 @@ __global__ void __launch_bounds__(NT, 448 / NT) row_step_pair(const Params<float
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long bars[kPairSlots];  // mbarriers of the TMA staging slots
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
-  // rows of this block: the first io.blocks_a row blocks have H rows, the rest io.fill_rows
-  const int by = blockIdx.y;
-  const bool tall = io.fill_rows <= 0 || by < io.blocks_a;
-  const int ya = tall ? by * H : io.blocks_a * H + (by - io.blocks_a) * io.fill_rows;
-  const int yb = min(ya + (tall ? H : io.fill_rows), P.ny);
+  int ya, yb;
+  block_rows(io, H, blockIdx.y, P.ny, &ya, &yb);
   if (pair_tile_simple<NT>(P, ya, yb, blockIdx.x))
     row_body_pair<ENERGY, NT, true>(P, io, ya, yb, blockIdx.x, bid, nblk, smem_raw, bars);
   else
