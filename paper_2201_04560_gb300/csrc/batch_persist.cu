@@ -145,24 +145,28 @@ __global__ void __launch_bounds__(NT, 384 / NT) persistent_batch(const PersistMe
     io.blocks_a = 0;
     io.fill_rows = 0;
     const int ya = by * M.H, yb = min(ya + M.H, P.ny);
-    const bool simple = pair_tile_simple<NT>(P, ya, yb, bx);
+    const int kind = pair_tile_kind<NT>(P, ya, yb, bx);
     const bool energy = M.energy_on && M.step0 + (long long)j >= M.iso_steps;
     unsigned *done = &ctl->done[e.mesh];
     const unsigned nblk = (unsigned)(M.gx * M.gy);
     // without gravity the mass is reduced on the launch's last step only (its counter and
     // partials then serve one step)
     const bool reduce = !M.local || j + 1 == (unsigned)(n_outer * M.sub);
+    const unsigned tile = (unsigned)e.tile, dv = j + 1;
     if (energy) {
-      if (simple)
-        row_body_pair<true, NT, true>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+      if (kind == 1)
+        row_body_pair<true, NT, true>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
+      else if (kind == 2)
+        row_body_pair<true, NT, true, true>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
       else
-        row_body_pair<true, NT, false>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+        row_body_pair<true, NT, false>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
     } else {
-      if (simple)
-        row_body_pair<false, NT, true>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1, reduce);
+      if (kind == 1)
+        row_body_pair<false, NT, true>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
+      else if (kind == 2)
+        row_body_pair<false, NT, true, true>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
       else
-        row_body_pair<false, NT, false>(P, io, ya, yb, bx, (unsigned)e.tile, nblk, smem_raw, bars, done, j + 1,
-                                        reduce);
+        row_body_pair<false, NT, false>(P, io, ya, yb, bx, tile, nblk, smem_raw, bars, done, dv, reduce);
     }
     if (M.local && threadIdx.x == 0) {  // this tile's step is complete (all its threads passed a barrier)
       __threadfence();

@@ -132,14 +132,16 @@ constexpr size_t row_step_pair_smem_bytes() {  // + 128: the staging base is ali
          128;
 }
 
-// Whether tile (bx, by) of H rows takes the specialisation without boundary logic: its rows and
-// their 3-row halo lie inside the domain, and its strip holds no column of a thermally
-// non-periodic x line (Dirichlet temperatures on x = 0 or x = nx - 1).
+// Specialisation a tile takes: 1 (no boundary logic) if its rows and their 3-row halo lie inside
+// the domain and its strip holds no column of a thermally non-periodic x line (Dirichlet
+// temperatures on x = 0 or x = nx - 1); 2 if the rows are inside but the strip holds such a
+// column (only the per-column Dirichlet checks remain); 0 otherwise.
 template <int NT>
-__device__ __forceinline__ bool pair_tile_simple(const Params<float> &P, int ya, int yb, int bx) {
+__device__ __forceinline__ int pair_tile_kind(const Params<float> &P, int ya, int yb, int bx) {
   const int g0 = bx * (2 * NT - 8) - 4, g1 = g0 + 2 * NT - 1;  // first and last strip column
   const bool xfix = (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (g0 <= 0 || g1 >= P.nx - 1);
-  return ya - 3 >= 1 && yb + 2 <= P.ny - 2 && !xfix;
+  if (ya - 3 < 1 || yb + 2 > P.ny - 2) return 0;
+  return xfix ? 2 : 1;
 }
 
 // The right-hand side of the energy equation (Eq. energy-equation) at a node, with the
@@ -157,7 +159,7 @@ struct PairHeun {
 // One tile of the step: strip bx (2 NT - 8 interior columns) and rows [ya, yb), CTA bid of
 // nblk for the mass reduction; `done` as in tile_mass_finalize.
 // reduce = false skips the mass reduction (a step whose domain mean nobody reads).
-template <bool ENERGY, int NT, bool SIMPLE>
+template <bool ENERGY, int NT, bool SIMPLE, bool XFIX = false>
 __device__ __forceinline__ void row_body_pair(const Params<float> &P, const StepIO &io, const int ya, const int yb, int bx,
                                               unsigned bid, unsigned nblk, unsigned char *smem_raw,
                                               unsigned long long *bars, unsigned *done = nullptr,
@@ -190,8 +192,8 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
   const int col0 = src0, col1 = src0 + 1;  // in-domain columns of the two lanes
   // a lane on a thermally non-periodic x line (e.g. a Dirichlet ring around a periodic box)
   // (never in the SIMPLE specialisation, which such strips do not take)
-  const bool col_fix =
-      !SIMPLE && (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) && (col0 == 0 || col1 == P.nx - 1);
+  const bool col_fix = (!SIMPLE || XFIX) && (P.tbc[0] != T_PERIODIC || P.tbc[1] != T_PERIODIC) &&
+                       (col0 == 0 || col1 == P.nx - 1);
   const long long plane = P.plane;
   const float rho_bar = (float)io.stats_in[0];
   const bool any_outflow = P.hbc[2] == OUTFLOW || P.hbc[3] == OUTFLOW;
@@ -571,7 +573,9 @@ __global__ void __launch_bounds__(NT, 448 / NT) row_step_pair(const Params<float
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
   int ya, yb;
   block_rows(io, H, blockIdx.y, P.ny, &ya, &yb);
-  if (pair_tile_simple<NT>(P, ya, yb, blockIdx.x))
+  // (strips with a Dirichlet x line take the general form here: a third specialisation in
+  // this kernel costs the others registers at its 128-register budget)
+  if (pair_tile_kind<NT>(P, ya, yb, blockIdx.x) == 1)
     row_body_pair<ENERGY, NT, true>(P, io, ya, yb, blockIdx.x, bid, nblk, smem_raw, bars);
   else
     row_body_pair<ENERGY, NT, false>(P, io, ya, yb, blockIdx.x, bid, nblk, smem_raw, bars);
