@@ -308,6 +308,34 @@ def test_persistent_batch_equals_separate_handles(ppl, th, ns, subs, outer, g):
         sims[k].close()
 
 
+def test_persistent_batch_dirichlet_ring(ppl, th):
+    # droplets in superheated vapour held by a Dirichlet temperature ring: every strip of these
+    # small meshes holds a Dirichlet x line, so the persistent kernel runs its tiles with rows
+    # inside the domain in the form that keeps only the per-column Dirichlet checks (the step
+    # kernel runs them in its general form); the energy equation switches on during the run
+    e = th["e"]
+    rv, rl, _ = th[0.8]
+    cfgs, ics = [], []
+    for n in (64, 128, 256):
+        c, ic = W.droplet_vaporization(e.Tc, rv, rl, thermo.sigma_for(e, 0.8 * e.Tc), nx=n, ny=n, R0=n / 4.0,
+                                       iso_steps=4, precision="fp32")
+        cfgs.append(c)
+        ics.append(ic)
+    subs = (1, 4, 16)
+    sims = [ppl.Simulation(c, *ic) for c, ic in zip(cfgs, ics)]
+    with ppl.Batch(sims, subs, mode="persistent") as b:
+        assert b.mode == "persistent"
+        b.step(3)
+    for k, (c, ic) in enumerate(zip(cfgs, ics)):
+        ref = ppl.Simulation(c, *ic)
+        ref.step(3 * subs[k])
+        np.testing.assert_array_equal(sims[k].populations(), ref.populations())
+        np.testing.assert_array_equal(sims[k].fields()["T"], ref.fields()["T"])
+        assert sims[k].norms()["flags"] == 0
+        ref.close()
+        sims[k].close()
+
+
 def test_persistent_batch_wait_limit_runs_out(ppl, th):
     # a zero wait limit makes the first dependency wait give up: the launch stops, the call
     # reports PPL_E_TIMEOUT, nothing faults, and the handles step normally after a reset
