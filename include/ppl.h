@@ -468,6 +468,13 @@ int ppl_tma_staging(const ppl_t *h);
  * context stays usable. Synchronous; PPL_E_INVAL for a limit out of range or a NULL flags. */
 int ppl_stall_probe(int64_t limit_ns, uint32_t *flags);
 
+/* Measured FP64 fused-multiply-add rate of the current device: a loop of independent DFMA
+ * chains on every SM (4 CTAs x 256 threads per SM, iters x 128 DFMAs per thread, 1 <= iters
+ * <= 1e6), timed with CUDA events after a warm-up; *dfma_per_s receives the FP64 FMA
+ * thread-operations per second (the FP64 step's roofline denominator). Synchronous, on a
+ * private stream; PPL_E_INVAL for iters out of range or a NULL result. */
+int ppl_fp64_rate(int32_t iters, double *dfma_per_s);
+
 /* Times `steps` (>= 1) steps at each candidate rows-per-CTA (the default and 1..256), for
  * each applicable step kernel (ppl_select_kernel), with CUDA events on the handle's
  * stream, keeps the fastest pair, and restores the state, step

@@ -605,6 +605,68 @@ int ppl_get_kernel(const ppl_t *h) {
   return h->var.fn[0] == step_variant_fp32_pair().fn[0] ? PPL_KERNEL_PAIR : PPL_KERNEL_COLUMN;
 }
 
+}  // extern "C"
+
+namespace {
+
+// FP64 FMA rate: eight independent chains of dependent DFMAs per thread, four 256-thread CTAs
+// per SM, so that the FP64 pipe (not latency) bounds the loop; the roofline denominator of the
+// FP64 step
+constexpr int kDfmaPerIter = 128;
+__global__ void dfma_loop(double *out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kDfmaPerIter / 8; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+
+cudaError_t launch_dfma_loop(double *out, int blocks, int threads, int iters, cudaStream_t stream) {
+  dfma_loop<<<blocks, threads, 0, stream>>>(out, iters, 0.999999, 1e-9);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int ppl_fp64_rate(int32_t iters, double *dfma_per_s) {
+  if (iters < 1 || iters > 1000000 || !dfma_per_s) return PPL_E_INVAL;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 4 * (sms > 0 ? sms : 1), threads = 256;
+  double *d = nullptr;
+  CK(cudaMalloc(&d, (size_t)blocks * threads * sizeof(double)));
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_dfma_loop(d, blocks, threads, 8, s);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = launch_dfma_loop(d, blocks, threads, iters, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(d);
+  CK(e);
+  *dfma_per_s = (double)blocks * threads * iters * kDfmaPerIter / (ms * 1e-3);
+  return PPL_OK;
+}
+
 int ppl_stall_probe(int64_t limit_ns, uint32_t *flags) {
   if (limit_ns <= 0 || limit_ns > 1000000000LL || !flags) return PPL_E_INVAL;
   unsigned *d = nullptr;

@@ -151,6 +151,8 @@ def load_library(build_if_missing: bool = True):
     L.ppl_tma_staging.restype = ctypes.c_int
     L.ppl_stall_probe.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32)]
     L.ppl_stall_probe.restype = ctypes.c_int
+    L.ppl_fp64_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.ppl_fp64_rate.restype = ctypes.c_int
     L.ppl_phase_area.argtypes = [H, _D, _D, _PD]
     L.ppl_relative_change.argtypes = [_PD, _PD, ctypes.c_int64, _PD]
     L.ppl_wall_heat_flux.argtypes = [H, ctypes.c_int, _PD]
@@ -200,6 +202,13 @@ def stall_probe(limit_ns: int) -> int:
     flags = ctypes.c_uint32(0)
     _check(load_library().ppl_stall_probe(int(limit_ns), ctypes.byref(flags)), "ppl_stall_probe")
     return int(flags.value)
+
+
+def fp64_rate(iters: int = 2000) -> float:
+    """Measured FP64 FMA thread-operations per second of the current device (ppl_fp64_rate)."""
+    r = ctypes.c_double(0.0)
+    _check(load_library().ppl_fp64_rate(int(iters), ctypes.byref(r)), "ppl_fp64_rate")
+    return float(r.value)
 
 
 def refine_a(a_base: float, n_base: int, n: int) -> float:

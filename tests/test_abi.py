@@ -63,6 +63,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.ppl_stall_probe(2_000_000_000, ctypes.byref(flags)) == ppl.PPL_E_INVAL
     assert lib.ppl_stall_probe(1000, None) == ppl.PPL_E_INVAL
     assert lib.ppl_tma_staging(None) == ppl.PPL_E_INVAL
+    # the FP64 rate probe checks its arguments before touching the device
+    r = ctypes.c_double(0.0)
+    assert lib.ppl_fp64_rate(0, ctypes.byref(r)) == ppl.PPL_E_INVAL
+    assert lib.ppl_fp64_rate(10, None) == ppl.PPL_E_INVAL
 
 
 def test_config_validation_rejects_bad_boundaries(lib):

@@ -270,6 +270,17 @@ def test_bounded_wait_reports_stall(sim_cls, th):
         assert s.norms()["flags"] == 0
 
 
+def test_fp64_rate_near_nominal(sim_cls):
+    # the FP64 roofline denominator: a DFMA loop on every SM runs at a large fraction of
+    # GB300's nominal 2 FP64 FMA per SM per clock (at the maximum SM clock of 2070 MHz)
+    import torch
+    from paper_2201_04560_gb300 import ppl as P
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rate = P.fp64_rate(500)
+    nominal = 2.0 * sms * 2.07e9
+    assert 0.3 * nominal < rate < 1.1 * nominal
+
+
 def test_pair_kernel_selection_rules(sim_cls, th):
     e = th["e"]
     rv, rl, _ = th[0.8]
