@@ -2,7 +2,7 @@
 arithmetic, populations stored as f_i - w_i rho_ref and T - T_ref) against the FP64 path on
 the same GPU, which matches the FP64 oracle to 1e-10 (tests/test_gpu_parity.py).
 
-Bound (the benchmark spec): 1e-4 relative in rho and T, 0.5 % in the coexistence densities. The
+Bound: 1e-4 relative in rho and T, 0.5 % in the coexistence densities. The
 relative error of a field is read in the paper's norm, sum |a - b| / sum |b| (the form of Eq.
 rel-diff-timestep): pointwise, at a diffuse interface a displacement dx of the front shows
 up as |grad rho| dx, about 2 dx in units of rho_v there, so a pointwise bound there is a

@@ -8,7 +8,7 @@ from oracle import oracle, thermo
 
 pytestmark = pytest.mark.gpu
 
-FP64_RTOL = 1e-10  # spec bound for the FP64 path (relative, rho and T)
+FP64_RTOL = 1e-10  # bound of the FP64 path against the oracle (relative, rho and T)
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +58,7 @@ def assert_fp64_parity(got, want, u_atol=1e-12):
 
 
 def test_static_droplet_fp64_5000_steps(sim_cls, th):
-    # isothermal static droplet, 64x64 periodic, 5,000 steps (the spec case)
+    # isothermal static droplet, 64x64 periodic, 5,000 steps
     e = th["e"]
     rv, rl, _ = th[0.8]
     cfg, ic = W.static_droplet(e.Tc, rv, rl, nx=64, ny=64, R0=16.0, width=3.0)
