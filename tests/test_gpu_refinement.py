@@ -141,13 +141,15 @@ def test_launch_shape_does_not_change_results(ppl, th, precision, rtol):
         s.close()
 
 
-def test_two_height_launch_shape(ppl, th):
+@pytest.mark.parametrize("g", [0.0, 3e-5])
+def test_two_height_launch_shape(ppl, th, g):
     # a grid large enough for the default two-column shape to follow one wave of tall row
-    # blocks with short ones (pool boiling, gravity off so that the mass sum does not enter,
-    # 2048 x 1800): results agree with one uniform wave to contraction-level rounding
+    # blocks with short ones (pool boiling, 2048 x 1800): results agree with one uniform wave
+    # to contraction-level rounding (with gravity, the per-CTA mass partials also round
+    # differently in the domain-mean density)
     e = th["e"]
     rv, rl, _ = th[0.86]
-    c, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=2048, ny=1800, g=0.0, precision="fp32")
+    c, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=2048, ny=1800, g=g, precision="fp32")
     s = ppl.Simulation(c, *ic)
     assert s.kernel == "pair"
     rows, ctas = s.launch()
