@@ -38,7 +38,8 @@
 // (one thread issues a 3-D tensor copy of the nine population rows and a 2-D copy of the
 // temperature row, completing on the slot's mbarrier, which all threads wait on) two rows
 // ahead; strips that wrap across the periodic x seam, and domains without tensor maps, use
-// per-thread 8-byte cp.async copies one row ahead, with the wrap applied per column.
+// per-thread 8-byte cp.async copies, also two rows ahead (one copy group per row; a thread
+// reads only the columns it copied), with the wrap applied per column.
 #pragma once
 
 #include "lane2.cuh"
@@ -249,11 +250,13 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
     for (int i = 0; i < 9; ++i) cp_async8(dst + i * SW, fin + i * plane + k);
     cp_async8(dst + 9 * SW, Tin + k);
   };
-  // rows ya - 3 and ya - 2 go out before the loop: by TMA both (two rows ahead), by cp.async
-  // the first (one row ahead; each iteration stages the next)
+  // rows ya - 3 and ya - 2 go out before the loop; each iteration then stages the row two
+  // ahead of its first stage, once the collision has read the slot it goes into (one
+  // cp.async group per row)
   stage_row(ya - 3, 0, stg + c2);
   cp_async_commit();
-  if (use_tma && n_it > 1) stage_row(ya - 2, 1, nullptr);
+  if (n_it > 1) stage_row(ya - 2, 1, stg + 10 * SW + c2);
+  cp_async_commit();
 
   // Slot roles: 0 holds rows q and q - 3, 1 rows q - 1 and q - 4, 2 rows q - 2 and q + 1.
   // Each iteration rotates the roles (0, 1, 2) <- (2, 0, 1).
@@ -277,11 +280,7 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
 
   for (int iq = 0; iq < n_it; ++iq) {
     const int q = ya - 3 + iq;
-    if (!use_tma) {
-      if (iq + 1 < n_it) stage_row(q + 1, k2, g2);
-      cp_async_commit();
-      cp_async_wait<1>();  // this thread's copies of row q have landed
-    }
+    if (!use_tma) cp_async_wait<1>();  // this thread's copies of row q have landed (row q + 1 may not)
     bool stalled = false;
     if (use_tma) stalled = !mbar_wait(bar_s + 8 * k0, (ph >> k0) & 1u);  // row q has landed
 
@@ -400,8 +399,10 @@ __device__ __forceinline__ void row_body_pair(const Params<float> &P, const Step
       __syncthreads();
     }
     // the slot of row q - 1 is free (its last reader, the collision, is past a barrier; before
-    // iteration 2 its row was read by the first stage only): row q + 2 goes into it
-    if (use_tma && iq + 2 < n_it) stage_row(q + 2, k1, nullptr);
+    // iteration 2 its row was read by the first stage only): row q + 2 goes into it (a thread's
+    // own copies only replace what the thread itself read)
+    if (iq + 2 < n_it) stage_row(q + 2, k1, g1);
+    if (!use_tma) cp_async_commit();
 
     // ---- S3: row q-2 (streaming, store of f; first Heun stage) ----
     if (iq >= 3) {
