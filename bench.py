@@ -146,12 +146,20 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def time_device(sim, steps, warmup, torch):
-    """Device time of `steps` fused steps (CUDA events on the launching stream)."""
+def time_device(sim, steps, warmup, torch, min_warm_s=0.0):
+    """Device time of `steps` fused steps (CUDA events on the launching stream), after `warmup`
+    untimed steps, continued in chunks until min_warm_s seconds have passed (a GPU that has been
+    idle runs its first tens of milliseconds of load below its maximum SM clock)."""
     stream = torch.cuda.Stream()
     sim.set_stream(stream)
+    t0 = time.perf_counter()
     sim.step_async(warmup)
     sim.sync()
+    warm_steps = warmup
+    while time.perf_counter() - t0 < min_warm_s:
+        sim.step_async(64)
+        sim.sync()
+        warm_steps += 64
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = sim.launch_count
     torch.cuda.synchronize()
@@ -160,7 +168,7 @@ def time_device(sim, steps, warmup, torch):
     end.record(stream)
     end.synchronize()
     sim.sync()
-    return start.elapsed_time(end) / 1e3, sim.launch_count - l0
+    return start.elapsed_time(end) / 1e3, sim.launch_count - l0, warm_steps
 
 
 def host_cpu():
@@ -339,10 +347,10 @@ def case_throughput():
             with ppl.Simulation(cfg, *ic) as sim:
                 if cfg["energy_on"]:
                     sim.step(cfg["iso_steps"])  # time the coupled step, past the isothermal start
-                dt, _ = time_device(sim, steps, 32, torch)
+                dt = time_device(sim, steps, 32, torch)[0]
                 rec = {"kernel": sim.kernel, "rows": sim.launch()[0], "mlups": nodes * steps / dt / 1e6}
                 rows, _ = sim.autotune(64)
-                dt2, _ = time_device(sim, steps, 32, torch)
+                dt2 = time_device(sim, steps, 32, torch)[0]
                 rec.update(autotuned_kernel=sim.kernel, autotuned_rows=rows, autotuned_mlups=nodes * steps / dt2 / 1e6)
             best = max(rec["mlups"], rec["autotuned_mlups"])
             rec["hbm_frac"] = best * 1e6 * BYTES_PER_NODE[prec] / 1e9 / hbm
@@ -435,13 +443,14 @@ def main():
         torch.cuda.synchronize()
         if sampler:
             sampler.start()
-        dt, launches = time_device(sim, steps, args.warmup, torch)
+        dt, launches, warm_steps = time_device(sim, steps, args.warmup, torch, min_warm_s=0.3 if prec == "fp32" else 0.0)
         clocks = sampler.stop() if sampler else None
         barrier()
         dt = max_over_ranks(dt, dist, "cuda")
         n = sim.norms()
         out[prec] = {"dt": dt, "steps": steps, "launches": launches, "clocks": clocks, "flags": n["flags"],
                      "mass": n["mass"], "kernel": sim.kernel, "rows_per_cta": sim.launch()[0],
+                     "warm_steps": warm_steps,
                      "staging": "tma" if sim.tma_staging else "cp.async"}
         if prec == "fp32" and not args.no_e2e:
             # end to end through the C ABI: pinned host inputs -> device, K steps, fields -> host
@@ -492,7 +501,9 @@ def main():
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "kernel": {"fp32": f32["kernel"], "fp64": f64["kernel"]},
                    "rows_per_cta": {"fp32": f32["rows_per_cta"], "fp64": f64["rows_per_cta"]},
-                   "fp32_row_staging": f32["staging"]},
+                   "fp32_row_staging": f32["staging"],
+                   "warmup_rule": "at least --warmup untimed steps, continued until 0.3 s of untimed steps have run "
+                                  "(the SM clock leaves its idle level); FP32 warm-up steps run: %d" % f32["warm_steps"]},
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                      "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,
