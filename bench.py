@@ -148,8 +148,8 @@ def measured_peaks():
 
 def time_device(sim, steps, warmup, torch, min_warm_s=0.0):
     """Device time of `steps` fused steps (CUDA events on the launching stream), after `warmup`
-    untimed steps, continued in chunks until min_warm_s seconds have passed (a GPU that has been
-    idle runs its first tens of milliseconds of load below its maximum SM clock)."""
+    untimed steps, continued in chunks until min_warm_s seconds have passed (on a GPU that has been
+    idle, the SM clock of a new context stayed ~4 % below its maximum for the first ~0.4 s of load)."""
     stream = torch.cuda.Stream()
     sim.set_stream(stream)
     t0 = time.perf_counter()
@@ -443,7 +443,7 @@ def main():
         torch.cuda.synchronize()
         if sampler:
             sampler.start()
-        dt, launches, warm_steps = time_device(sim, steps, args.warmup, torch, min_warm_s=0.3 if prec == "fp32" else 0.0)
+        dt, launches, warm_steps = time_device(sim, steps, args.warmup, torch, min_warm_s=1.0 if prec == "fp32" else 0.0)
         clocks = sampler.stop() if sampler else None
         barrier()
         dt = max_over_ranks(dt, dist, "cuda")
@@ -502,8 +502,9 @@ def main():
                    "kernel": {"fp32": f32["kernel"], "fp64": f64["kernel"]},
                    "rows_per_cta": {"fp32": f32["rows_per_cta"], "fp64": f64["rows_per_cta"]},
                    "fp32_row_staging": f32["staging"],
-                   "warmup_rule": "at least --warmup untimed steps, continued until 0.3 s of untimed steps have run "
-                                  "(the SM clock leaves its idle level); FP32 warm-up steps run: %d" % f32["warm_steps"]},
+                   "warmup_rule": "at least --warmup untimed steps, continued until 1 s of untimed steps have run "
+                                  "(a freshly started context runs its first ~0.4 s below the maximum SM clock); "
+                                  "FP32 warm-up steps run: %d" % f32["warm_steps"]},
         "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
                      "traffic": kernel_traffic(), "peak_kind": peak_kind, "bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": mlups64, "unit": "MLUPS", "steps": f64["steps"], "ms_per_step": per_launch64 * 1e3,
