@@ -160,8 +160,11 @@ int ppl_reset(ppl_t *h, const double *rho0, const double *ux0, const double *uy0
 int ppl_set_stream(ppl_t *h, void *cuda_stream);
 
 /* Advance nsteps >= 0 time steps (one fused kernel launch per step, replayed from CUDA
- * graphs in chunks), then synchronise the stream and check the device status word:
- * PPL_E_NUMERIC if any flag is set. */
+ * graphs of 32, 16, 8, 4 and 2 steps, at most one step launched on its own), then
+ * synchronise the stream and check the device status word: PPL_E_NUMERIC if any flag is
+ * set. The first call that can use a graph captures all of them (for the current energy
+ * setting), so that call takes longer. Inside a stream capture of the caller's, steps are
+ * launched one by one into that capture. */
 int ppl_step(ppl_t *h, int64_t nsteps);
 
 /* As ppl_step but returns right after enqueueing; no status check, no synchronisation. */

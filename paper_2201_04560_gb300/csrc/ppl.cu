@@ -505,15 +505,15 @@ int launch_step(ppl_sim *h, bool energy) {
 
 bool energy_at(const ppl_sim *h, int64_t step) { return h->cfg.energy_on && step >= h->cfg.iso_steps; }
 
-int capture_graph(ppl_sim *h, int e) {
-  // capture kGraphSteps launches starting from parity 0; host bookkeeping is restored
+// capture kGraphLen[k] launches starting from parity p; host bookkeeping is restored
+static int capture_graph(ppl_sim *h, int e, int p, int k) {
   const int cur0 = h->cur;
   const int64_t step0 = h->step, l0 = h->launches;
-  h->cur = 0;
+  h->cur = p;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int rc = PPL_OK;
-  for (int i = 0; i < kGraphSteps && rc == PPL_OK; ++i) rc = launch_step(h, e != 0);
+  for (int i = 0; i < kGraphLen[k] && rc == PPL_OK; ++i) rc = launch_step(h, e != 0);
   cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
   h->cur = cur0;
   h->step = step0;
@@ -523,10 +523,32 @@ int capture_graph(ppl_sim *h, int e) {
     return rc;
   }
   CK(ce);
-  ce = cudaGraphInstantiate(&h->graph[e], g, 0);
+  ce = cudaGraphInstantiate(&h->graph[e][p][k], g, 0);
   cudaGraphDestroy(g);
   CK(ce);
   return PPL_OK;
+}
+
+// every length and both parities of one energy setting, captured together on first use (so
+// that the first run long enough for a graph, typically a warm-up, pays for all of them)
+static int capture_graphs(ppl_sim *h, int e) {
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 5; ++k)
+      if (!h->graph[e][p][k]) {
+        const int rc = capture_graph(h, e, p, k);
+        if (rc) return rc;
+      }
+  return PPL_OK;
+}
+
+void drop_graphs(ppl_sim *h) {
+  for (auto &ep : h->graph)
+    for (auto &pk : ep)
+      for (auto &g : pk)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
 }
 
 template <typename real>
@@ -649,8 +671,7 @@ int check_status(ppl_sim *h) {
 }
 
 void free_all(ppl_sim *h) {
-  for (int e = 0; e < 2; ++e)
-    if (h->graph[e]) cudaGraphExecDestroy(h->graph[e]);
+  drop_graphs(h);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->f[i]);
     cudaFree(h->T[i]);
@@ -900,18 +921,24 @@ int ppl_set_stream(ppl_t *h, void *cuda_stream) {
 int ppl_step_async(ppl_t *h, int64_t nsteps) {
   if (!h || nsteps < 0) return PPL_E_INVAL;
   int64_t left = nsteps;
+  // inside a stream capture of the caller every step is launched on its own (the capture
+  // records them); no graph is captured or replayed
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(h->stream, &cs));
+  const int kmin = cs == cudaStreamCaptureStatusNone ? 0 : 5;
   while (left > 0) {
     const bool e = energy_at(h, h->step);
-    const bool uniform = energy_at(h, h->step + kGraphSteps - 1) == e;
-    if (h->cur == 0 && left >= kGraphSteps && uniform) {
-      if (!h->graph[e ? 1 : 0]) {
-        int rc = capture_graph(h, e ? 1 : 0);
+    int k = kmin;  // the longest graph that fits and does not cross the start of the energy equation
+    while (k < 5 && (left < kGraphLen[k] || energy_at(h, h->step + kGraphLen[k] - 1) != e)) ++k;
+    if (k < 5) {
+      if (!h->graph[e][h->cur][k]) {
+        int rc = capture_graphs(h, e ? 1 : 0);
         if (rc) return rc;
       }
-      CK(cudaGraphLaunch(h->graph[e ? 1 : 0], h->stream));
-      h->step += kGraphSteps;
-      h->launches += kGraphSteps;
-      left -= kGraphSteps;
+      CK(cudaGraphLaunch(h->graph[e][h->cur][k], h->stream));
+      h->step += kGraphLen[k];
+      h->launches += kGraphLen[k];
+      left -= kGraphLen[k];
     } else {
       int rc = launch_step(h, e);
       if (rc) return rc;

@@ -41,7 +41,8 @@ struct ppl_sim {
   int64_t launches = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [energy], captured from parity 0
+  // captured step sequences [energy][starting parity][length index] (lengths kGraphLen)
+  cudaGraphExec_t graph[2][2][5] = {};
   StepVariant var;
   dim3 grid;
   int rows_per_cta = 0;
@@ -59,7 +60,11 @@ struct ppl_sim {
 
 namespace ppl_host {
 
-constexpr int kGraphSteps = 32;  // steps per captured CUDA graph (even: ping-pong parity returns)
+// steps per captured CUDA graph, longest first (even: the ping-pong parity returns); a run
+// of n steps replays the longest graphs that fit and launches at most one step on its own
+constexpr int kGraphSteps = 32;
+constexpr int kGraphLen[5] = {32, 16, 8, 4, 2};
+void drop_graphs(ppl_sim *h);
 
 int cuda_err(cudaError_t e);
 #define CK(x)                                   \

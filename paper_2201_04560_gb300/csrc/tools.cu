@@ -569,11 +569,7 @@ int ppl_host::apply_shape(ppl_sim *h, int H, int fill_rows) {
     h->partials = p;
     h->npart = need;
   }
-  for (int e = 0; e < 2; ++e)
-    if (h->graph[e]) {
-      cudaGraphExecDestroy(h->graph[e]);
-      h->graph[e] = nullptr;
-    }
+  drop_graphs(h);
   h->rows_per_cta = H;
   h->fill_rows = fill_rows > 0 ? fill_rows : 0;
   h->tall_blocks = tall;

@@ -167,6 +167,55 @@ def test_checkpoint_resume_is_bit_identical(sim_cls, th, tmp_path):
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_equals_single_launches(sim_cls, th, prec):
+    # runs of 5, 20, 3 and 37 steps replay captured graphs of 32 ... 2 steps from either
+    # ping-pong parity, across the start of the energy equation (iso_steps = 30); one step at a
+    # time launches every step on its own: the states agree bit for bit, and the step count
+    # and the launch count are those of 65 steps
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=64, ny=72, g=3e-5, precision=prec)
+    cfg["iso_steps"] = 30
+    a = sim_cls(cfg, *ic)
+    b = sim_cls(cfg, *ic)
+    for n in (5, 20, 3, 37):
+        a.step(n)
+    for _ in range(65):
+        b.step(1)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    np.testing.assert_array_equal(a.fields()["T"], b.fields()["T"])
+    assert a.norms()["step"] == b.norms()["step"] == 65
+    assert a.launch_count == b.launch_count == 65
+    a.close()
+    b.close()
+
+
+def test_steps_captured_into_a_callers_graph(sim_cls, th):
+    # inside the caller's stream capture the steps are launched one by one into it (no graph
+    # of the library's own is captured or replayed there); one replay of the caller's graph
+    # equals six steps taken directly
+    import torch
+    e = th["e"]
+    rv, rl, _ = th[0.86]
+    cfg, ic = W.pool_boiling(e.Tc, rv, rl, 0.1032, nx=64, ny=72, g=3e-5, precision="fp32")
+    a = sim_cls(cfg, *ic)
+    b = sim_cls(cfg, *ic)
+    s = torch.cuda.Stream()
+    a.set_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        a.step_async(6)
+    g.replay()
+    torch.cuda.synchronize()
+    a.sync()
+    b.step(6)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    np.testing.assert_array_equal(a.fields()["T"], b.fields()["T"])
+    a.close()
+    b.close()
+
+
 def test_invalid_initial_state_is_rejected(sim_cls):
     from paper_2201_04560_gb300 import PplError
     e = thermo.PR()
